@@ -1,0 +1,348 @@
+"""Benchmark: Mcell-stage updates/s of the WENO5-JS Euler residual + SSP-RK3
+step on one GB300, FP32-bulk and FP64, with the roofline of the dominant
+kernel, the L1 error reached, an end-to-end number through host buffers, and
+the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload 2d|3d]
+
+A step is one SSP-RK3 step (three stages, each a full residual over the grid
+plus the stage combination) of the 2D periodic density wave on 2048^2
+(rho = 1 + 0.2 sin(pi (x + y)), u = v = 1, p = 1 on [0,2)^2), synthetic.
+Under torchrun every rank runs its own independent grid (replicas, weak
+scaling); there is no data-path collective.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "2d": dict(dim=2, n=(2048, 2048), name="2d_density_wave_2048sq"),
+    "3d": dict(dim=3, n=(256, 256, 256), name="3d_density_wave_256cube"),
+}
+
+# Algorithmic FP64/FP32 operation counts of the scheme as the paper writes it
+# (each +, -, *, /, sqrt one flop), per cell, from the oracle's formulas:
+#   WENO5 value: 68; interface flux per component: 2 * 68 + 1 = 137;
+#   point flux + LF split per direction: 9 D + 18; flux difference per
+#   component: 3; stage combination per field: 4 (stage average);
+#   wavespeed max per cell: 6 D + 10.
+def flops_sweep(D, last):
+    nf = D + 2
+    f = nf * 137 + 9 * D + 18 + 3 * nf
+    if last:
+        f += nf + 4 * nf + 6 * D + 10  # accumulator add, stage combination, wavespeed
+    return f
+
+
+def flops_cell_stage(D):
+    return sum(flops_sweep(D, d == D - 1) for d in range(D))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP32 FFMA pipe: 152 SMs x 128 lanes x 2 flop at the 2070 MHz maximum clock;
+# FP64: the nominal 1.25 TFLOP/s of GB300.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        smax = max(num(r[2]) or 0 for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(seconds=12.0):
+    """The oracle (plain FP64 C, one thread) on a bounded sample of the same
+    workload: SSP-RK3 steps of the 2D density wave on 256^2."""
+    import oracle as O
+    from paper_2405_12301_gb300 import inputs as I
+    n = (256, 256)
+    cfg = O.Cfg(dim=2, n=n, lo=(0.0, 0.0), hi=(2.0, 2.0))
+    U = I.density_wave(2, n)
+    dt = O.cfl_dt(cfg, U, 0.5)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        U = O.ssprk3_step(cfg, U, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    value = n[0] * n[1] * 3 * steps / el / 1e6
+    return {"value": value, "unit": "Mcell-stage/s", "cores": 1, "kind": "oracle",
+            "sample": "%d SSP-RK3 steps of the 2D density wave on 256^2 (%.1f s, 1 thread)" % (steps, el)}
+
+
+def reference_arm(args, rank):
+    """--impl reference: the oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2405_12301_gb300 import inputs as I
+    w = WORKLOADS[args.workload]
+    n = (256, 256) if w["dim"] == 2 else (32, 32, 32)
+    lo, hi = (0.0,) * w["dim"], (2.0,) * w["dim"]
+    cfg = O.Cfg(dim=w["dim"], n=n, lo=lo, hi=hi)
+    U = I.density_wave(w["dim"], n)
+    dt = O.cfl_dt(cfg, U, 0.5)
+    for _ in range(args.warmup):
+        U = O.ssprk3_step(cfg, U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = O.ssprk3_step(cfg, U, dt)
+    el = time.perf_counter() - t0
+    cells = 1
+    for x in n:
+        cells *= x
+    v = cells * 3 * args.steps / el / 1e6
+    sample = "each step: one SSP-RK3 step of the same density wave on %s (oracle, 1 thread)" % "x".join(map(str, n))
+    print(json.dumps({
+        "impl": "reference", "metric": "Mcell-stage updates/s", "value": v, "unit": "Mcell-stage/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "sample_grid": list(n)},
+        "cpu_baseline": {"value": v, "unit": "Mcell-stage/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "Mcell-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def accuracy(weno, I, torch, dim=2, N=256):
+    """L1 error of rho against the exact advected wave at t = 2, FP64 and
+    FP32-bulk on the GPU, and the FP32 floor (L1 difference of the two runs)."""
+    import numpy as np
+    n = (N,) * dim
+    U0 = I.density_wave(dim, n)
+    ex = I.density_wave(dim, n, t=2.0)
+    out = {}
+    for prec in (weno.FP64, weno.FP32_BULK):
+        s = weno.Solver(dim, n, (0.0,) * dim, (2.0,) * dim, precision=prec)
+        Ud = torch.from_numpy(U0).cuda()
+        s.set_time(0.0)
+        s.run(Ud, 2.0, graph_steps=32)
+        out[prec] = Ud.cpu().numpy()
+        s.close()
+    e64 = float(np.abs(out[weno.FP64][0] - ex[0]).mean())
+    e32 = float(np.abs(out[weno.FP32_BULK][0] - ex[0]).mean())
+    floor = float(np.abs(out[weno.FP32_BULK][0] - out[weno.FP64][0]).mean())
+    return {"grid": list(n), "t": 2.0, "l1_rho_fp64": e64, "l1_rho_fp32_bulk": e32, "fp32_floor_l1": floor}
+
+
+def time_precision(weno, I, torch, w, prec, steps, warmup, dist, world):
+    """Timed region: `steps` SSP-RK3 steps, every kernel bracketed by CUDA events
+    on the launch stream.  Returns ms, per-kind kernel totals and launches."""
+    dim, n = w["dim"], w["n"]
+    s = weno.Solver(dim, n, (0.0,) * dim, (2.0,) * dim, precision=prec)
+    U = torch.from_numpy(I.density_wave(dim, n)).cuda()
+    s.set_time(0.0)
+    s.run(U, 1e30, max_steps=warmup, graph_steps=0)
+    s.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record()
+    taken = s.run(U, 1e30, max_steps=steps, graph_steps=0)
+    ev1.record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kms, kn, launches = s.profile_read()
+    s.profile_enable(False)
+    # graph mode, for reference (same steps, CUDA graph of 8 steps)
+    torch.cuda.synchronize()
+    ev0.record()
+    s.run(U, 1e30, max_steps=steps, graph_steps=8)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_graph = ev0.elapsed_time(ev1)
+    s.close()
+    assert taken == steps
+    return ms, kms, kn, launches, ms_graph
+
+
+def roofline(w, prec_bulk, kms, kn, cells):
+    D = w["dim"]
+    kinds = [k for k in range(6) if kn[k] > 0]
+    k = max(kinds, key=lambda i: kms[i])
+    last = k >= 3
+    per_launch_ms = kms[k] / kn[k]
+    flops = cells * flops_sweep(D, last)
+    achieved = flops / (per_launch_ms * 1e-3) / 1e12
+    peak = PEAK_FP32_TFLOPS if prec_bulk else PEAK_FP64_TFLOPS
+    names = KIND_NAMES
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": names[k], "ms_per_launch": per_launch_ms,
+            "pipe": "fp32" if prec_bulk else "fp64",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if prec_bulk
+            else "nominal GB300 FP64 1.25 TFLOP/s"}
+
+
+KIND_NAMES = ["sweep_x", "sweep_y", "sweep_z", "sweep_x_last", "sweep_y_last", "sweep_z_last", "alpha", "small"]
+
+
+def kernel_table(kms, kn):
+    return {KIND_NAMES[k]: [kms[k] / kn[k], kn[k]] for k in range(len(kms)) if kn[k] > 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_12301_gb300 import inputs as I
+    from paper_2405_12301_gb300 import weno
+
+    w = WORKLOADS[args.workload]
+    cells = 1
+    for x in w["n"]:
+        cells *= x
+    clocks = Clocks(local)
+    ms, kms, kn, launches, ms_graph = time_precision(weno, I, torch, w, weno.FP32_BULK, args.steps, args.warmup,
+                                                      dist, world)
+    ms64, kms64, kn64, launches64, ms64_graph = time_precision(weno, I, torch, w, weno.FP64, max(3, args.steps // 4),
+                                                                args.warmup, dist, world)
+    clk = clocks.stop()
+
+    def mx(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms, ms64 = mx(ms), mx(ms64)
+    value = cells * 3 * args.steps * world / (ms * 1e-3) / 1e6
+    steps64 = max(3, args.steps // 4)
+    value64 = cells * 3 * steps64 * world / (ms64 * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory, steps, and copies it back
+    s = weno.Solver(w["dim"], w["n"], (0.0,) * w["dim"], (2.0,) * w["dim"], precision=weno.FP32_BULK)
+    Uh = torch.from_numpy(I.density_wave(w["dim"], w["n"])).pin_memory()
+    s.set_time(0.0)
+    for _ in range(2):
+        s.run_host(Uh, 1e30, max_steps=1, graph_steps=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.run_host(Uh, 1e30, max_steps=1, graph_steps=0)
+    e2e_s = mx(time.perf_counter() - t0)
+    s.close()
+    state_bytes = Uh.numel() * 8
+    e2e = {"value": cells * 3 * args.steps * world / e2e_s / 1e6, "unit": "Mcell-stage/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "api": "weno_run_host (pinned host state, one step per call)"}
+
+    acc = accuracy(weno, I, torch) if rank == 0 else None
+    rl = roofline(w, True, kms, kn, cells)
+    rl64 = roofline(w, False, kms64, kn64, cells)
+    step_tflops = value * 1e6 * flops_cell_stage(w["dim"]) / 1e12 / world
+    line = {
+        "metric": "Mcell-stage updates/s", "value": value, "unit": "Mcell-stage/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 bulk (f64 state)", "data": "synthetic",
+        "config": {"workload": w["name"], "grid": list(w["n"]), "precision": "fp32_bulk",
+                   "timestep": "SSP-RK3, CFL 0.5", "l2_policy": "inputs larger than L2 (state %d MB x 3 buffers)" %
+                   (cells * (w["dim"] + 2) * 8 // 2 ** 20), "launch": "plain launches with per-kernel events"},
+        "roofline": rl,
+        "step_roofline": {"achieved": step_tflops, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                          "frac": step_tflops / PEAK_FP32_TFLOPS,
+                          "flops_per_cell_stage": flops_cell_stage(w["dim"])},
+        "kernels_ms_per_launch": kernel_table(kms, kn),
+        "graph_ms_per_step": ms_graph / args.steps,
+        "fp64": {"value": value64, "unit": "Mcell-stage/s", "steps": steps64, "ms_per_step": ms64 / steps64,
+                 "graph_ms_per_step": ms64_graph / steps64, "roofline": rl64,
+                 "kernels_ms_per_launch": kernel_table(kms64, kn64)},
+        "accuracy": acc,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * weno_gb300.h -- C ABI of the GB300 (sm_103a) WENO5-JS residual library
+ * for the compressible Euler equations.
+ *
+ * The library computes, on one GPU, the semi-discrete finite-difference
+ * residual of Danis et al., "Tensor-Train WENO Scheme for Compressible
+ * Flows":
+ *   L(U) = -(F^_{i+1/2} - F^_{i-1/2})/dx - (G^...)/dy - (H^...)/dz
+ * (Sec. 4.1, Eq. euler-system-for-loop) with the Euler fluxes of Sec. 2.1,
+ * global Lax-Friedrichs splitting f(+/-) = (f(u) +/- alpha u)/2 (Sec. 2.2,
+ * Eq. lax-friedrichs; alpha = max(|u| + a), Sec. 4.3), fifth-order WENO-JS
+ * reconstruction of f(+) and of its mirror image f(-) (Sec. 2.2), three ghost
+ * layers per side (Sec. 4.5), and the SSP-RK3 time step of Eq. (tt-ssprk3)
+ * without rounding, with dt = lambda h / max(alpha) (Eq. cfl-other).
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns a weno_status (int).  On failure the handle's
+ *     weno_last_error() text says why.  Nothing is ever computed on the host:
+ *     a combination the GPU path does not implement returns
+ *     WENO_ERR_UNSUPPORTED.
+ *   - Memory: every array argument is caller-owned.  Unless a parameter says
+ *     "host", it is a device pointer of the current CUDA device.  The library
+ *     owns only the scratch it allocates in weno_init (stage states, residual
+ *     accumulator, reduction partials, control block), freed by weno_destroy.
+ *   - State layout: FP64 structure-of-arrays U[f][k][j][i], i (x) fastest,
+ *     interior cells only, contiguous; nf = dim + 2 fields in the order
+ *     rho, rho u, (rho v), (rho w), rho E.  Ghost cells are not stored; the
+ *     kernels synthesise them from the boundary rule.
+ *   - Streams: work is enqueued asynchronously on the handle's stream.
+ *     Device-side conditions (non-physical state: non-finite values, rho <= 0,
+ *     p <= 0) are latched in a device status word and reported by the next
+ *     synchronising call (weno_sync, weno_get_time, weno_sums, weno_run,
+ *     weno_run_host) as WENO_ERR_NONPHYSICAL.
+ *   - Grid: cell-centred, x_i = lo + (i + 1/2) h, h = (hi - lo) / n.
+ */
+#ifndef WENO_GB300_H
+#define WENO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct weno_ctx *weno_handle;
+
+typedef enum {
+    WENO_OK = 0,
+    WENO_ERR_ARG = 1,          /* invalid argument (null pointer, size, enum) */
+    WENO_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    WENO_ERR_NONPHYSICAL = 3,  /* device saw NaN/Inf, rho <= 0 or p <= 0 */
+    WENO_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    WENO_ERR_UNSUPPORTED = 5   /* combination not implemented on the GPU */
+} weno_status;
+
+/* Boundary rules (Sec. 4.5).  PERIODIC: ghosts copy the opposite interior
+ * end.  TRANSMISSIVE: ghosts copy the nearest interior cell (zero-order
+ * extrapolation; not defined in the paper).  REFLECTIVE: symmetry plane,
+ * q(-2+l) = q(3-l) for l = 0,1,2 with the normal momentum negated. */
+typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_TRANSMISSIVE = 1, WENO_BC_REFLECTIVE = 2 } weno_bc;
+
+/* WENO_FP64: every operation in FP64.  WENO_FP32_BULK: point fluxes, splitting
+ * and reconstruction in FP32 on values taken relative to a reference state of
+ * each tile line (stencil differences are formed before rounding to FP32);
+ * the state, its stage combination and the conservation sums stay FP64. */
+typedef enum { WENO_FP64 = 0, WENO_FP32_BULK = 1 } weno_precision;
+
+/* Lax-Friedrichs constant: one global alpha = max over cells of |u| + a
+ * (Sec. 4.3, Eq. cfl-other).  WENO_ALPHA_PER_DIR (max |u_d| + a per
+ * direction, Eq. lax-friedrichs read per direction) is declared for the
+ * interface but returns WENO_ERR_UNSUPPORTED. */
+typedef enum { WENO_ALPHA_GLOBAL_NORM = 0, WENO_ALPHA_PER_DIR = 1 } weno_alpha_mode;
+
+typedef struct {
+    int32_t dim;     /* 1, 2 or 3 */
+    int32_t reserved;
+    int64_t n[3];    /* interior cells per direction; n[d] = 1 for d >= dim */
+    double lo[3];    /* domain [lo, hi) per direction */
+    double hi[3];
+} weno_grid;
+
+typedef struct {
+    double gamma;        /* ratio of specific heats (1.4 for air) */
+    double eps_weno;     /* WENO epsilon in alpha_r = d_r / (beta_r + eps)^2 */
+    double cfl;          /* lambda in dt = lambda h / max(alpha); h = min_d h_d */
+    int32_t bc[3][2];    /* weno_bc per direction, [low side, high side] */
+    int32_t precision;   /* weno_precision */
+    int32_t alpha_mode;  /* weno_alpha_mode */
+} weno_params;
+
+/* Creates a handle for one grid and parameter set, allocates its scratch
+ * (three FP64 state-sized buffers and one residual accumulator) and binds
+ * cuda_stream (a cudaStream_t; NULL = the legacy default stream).  grid may be
+ * NULL for a handle used only by weno_cross_eval.  Errors: WENO_ERR_ARG for a
+ * bad grid/parameter, WENO_ERR_CUDA if allocation fails (nothing is leaked). */
+int weno_init(weno_handle *out, const weno_grid *grid, const weno_params *params, void *cuda_stream);
+
+/* Frees the handle and its scratch (synchronises its stream first). */
+int weno_destroy(weno_handle h);
+
+/* Rebinds the stream used by later calls; drops any captured CUDA graph. */
+int weno_set_stream(weno_handle h, void *cuda_stream);
+
+/* alpha_dev[0] = max over interior cells of |u| + sqrt(gamma p / rho) of U
+ * (Sec. 4.3), computed in the handle's precision.  alpha_dev: device double. */
+int weno_alpha(weno_handle h, const double *U, double *alpha_dev);
+
+/* R = L(U) (Sec. 4.1, Eq. euler-system-for-loop), with alpha recomputed from U.
+ * U, R: device FP64 [nf][nz][ny][nx]; R must not alias U.  alpha_dev (device
+ * double, may be NULL) receives the alpha used. */
+int weno_rhs(weno_handle h, const double *U, double *R, double *alpha_dev);
+
+/* Sets / reads the handle's simulation time (a device scalar, so that captured
+ * graphs need no host round trip).  weno_get_time synchronises the stream and
+ * also returns the number of steps taken since the last weno_set_time; it
+ * returns WENO_ERR_NONPHYSICAL if the device latched a non-physical state. */
+int weno_set_time(weno_handle h, double t);
+int weno_get_time(weno_handle h, double *t, int64_t *steps);
+
+/* Advances U in place by one SSP-RK3 step (Eq. tt-ssprk3 without rounding):
+ *   U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1)); U' = 1/3 U + 2/3 (U2 + dt L(U2)),
+ * alpha recomputed from every stage's state.  dt > 0: that step size;
+ * dt <= 0: dt = cfl h / alpha(U) (Eq. cfl-other).  Either way the step is
+ * shortened so that the handle's time does not pass t_end, and it is a no-op
+ * once the time has reached t_end.  The time and step count advance on the
+ * device.  U: device FP64, overwritten. */
+int weno_ssprk3_step(weno_handle h, double *U, double t_end, double dt);
+
+/* Up to max_steps SSP-RK3 steps (as weno_ssprk3_step) until the handle's time
+ * reaches t_end.  Steps are launched as CUDA graphs of graph_steps steps
+ * (graph_steps <= 0: plain launches); the graph is captured on first use for a
+ * given U and reused.  alpha is carried from the last stage of one step to the
+ * next.  Synchronises; *steps_out (host, may be NULL) receives the number of
+ * steps taken by this call. */
+int weno_run(weno_handle h, double *U, double t_end, double dt, int64_t max_steps, int32_t graph_steps,
+             int64_t *steps_out);
+
+/* As weno_run, for a state held in HOST memory (pinned memory is fastest):
+ * copies U_host to the device, runs, and copies the result back into U_host. */
+int weno_run_host(weno_handle h, double *U_host, double t_end, double dt, int64_t max_steps,
+                  int32_t graph_steps, int64_t *steps_out);
+
+/* Conservation sums: sums_host[f] = sum over interior cells of U[f], FP64, in a
+ * fixed order (bitwise reproducible).  Synchronises.  sums_host: host, nf. */
+int weno_sums(weno_handle h, const double *U, double *sums_host);
+
+/* Synchronises the handle's stream; returns the latched device status. */
+int weno_sync(weno_handle h);
+
+/* Kernel timing.  While enabled, calls that launch kernels without a CUDA graph
+ * (weno_rhs, weno_ssprk3_step, weno_run with graph_steps <= 0) record a CUDA
+ * event pair around every kernel on the handle's stream; weno_profile_read
+ * (synchronises) adds the elapsed times up per kernel kind:
+ *   kind 0..2: sweep of direction d that stores/adds to the accumulator,
+ *   kind 3..5: last sweep of a stage (direction d, stage combination or L(U)),
+ *   kind 6: wavespeed max, kind 7: step control and other small kernels.
+ * ms and launches (host arrays of WENO_PROFILE_KINDS) receive the totals since
+ * the last enable; *total_launches counts every kernel this handle launched
+ * (graphs included) since the last enable. */
+enum { WENO_PROFILE_KINDS = 8 };
+int weno_profile_enable(weno_handle h, int32_t enable);
+int weno_profile_read(weno_handle h, double *ms, int64_t *launches, int64_t *total_launches);
+
+/* Text of the last error on this handle (never NULL; static storage of the
+ * handle, valid until the next call on it).  h may be NULL: then it describes
+ * the last weno_init failure of this thread. */
+const char *weno_last_error(weno_handle h);
+
+/* ------------------------------------------------------------------------
+ * Pointwise evaluation at TT-cross sample points (Sec. 4.2-4.3, Algorithms 1
+ * and 2): for each sample of a cross sweep, the 7-point stencil along the flux
+ * direction is contracted out of the TT cores (Eq. TT_def), and the
+ * Lax-Friedrichs split, WENO5 reconstruction and flux difference give the
+ * direction's residual contribution -(F^_{i+1/2} - F^_{i-1/2}) / h.
+ * ------------------------------------------------------------------------ */
+
+/* One 3D Euler state in TT format.  core[f][m] is the device FP32 core of mode
+ * m of field f, shaped [n_m][r_{m-1}][r_m] (r_0 = r_3 = 1), so that
+ * U_f(i,j,k) = sum_{a,b} core[f][0][i][0][a] core[f][1][j][a][b] core[f][2][k][b][0].
+ * Ghost rows (Sec. 4.5, core-level periodic / symmetry fill) are not stored:
+ * row indices outside [0, n_m) are mapped by bc[m]. */
+typedef struct {
+    int32_t n[3];
+    int32_t r[2];
+    int32_t reserved;
+    const float *core[5][3];
+    double h[3];       /* spacing per mode */
+    double alpha;      /* LF constant (the paper estimates it with tt_max_abs) */
+    int32_t bc[3][2];  /* weno_bc per mode, [low, high] */
+} weno_tt_instance;
+
+/* The samples of one cross sweep of one instance over `mode`: every
+ * (left l, index i of mode, right r), left/right being the rank index sets of
+ * TT-cross.  left: device int32 [n_left][mode] (multi-indices over modes <
+ * mode; n_left = 1 and NULL when mode = 0); right: device int32
+ * [n_right][2 - mode] (over modes > mode; n_right = 1 and NULL when mode = 2).
+ * out: device [5][n_left][n_mode][n_right], FP32 (FP64 with
+ * WENO_CROSS_FP64_CHECK). */
+typedef struct {
+    int32_t instance;
+    int32_t mode;
+    int32_t flux_dir;
+    int32_t reserved;
+    int64_t n_left;
+    int64_t n_right;
+    const int32_t *left;
+    const int32_t *right;
+    void *out;
+} weno_fiber_set;
+
+enum { WENO_CROSS_FP64_CHECK = 1 };
+
+/* Evaluates every fiber set in one persistent launch on the handle's stream.
+ * inst, sets: HOST arrays (copied into the handle's scratch; the device arrays
+ * they point to must stay valid until the work completes).  Uses the handle's
+ * gamma and eps_weno.  flags: WENO_CROSS_FP64_CHECK evaluates in FP64 and
+ * writes FP64 outputs.  Errors: WENO_ERR_ARG for inconsistent sizes or ranks
+ * above 64. */
+int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, const weno_fiber_set *sets,
+                    int32_t n_sets, int32_t flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WENO_GB300_H */

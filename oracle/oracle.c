@@ -398,9 +398,14 @@ int64_t o_run(const ocfg *c, double *U, double t0, double t_end, double cfl, dou
             double dtc = dt_coef * pow(h, dt_pow);
             if (dtc < dt) dt = dtc;
         }
-        if (t + dt > t_end) dt = t_end - t;
+        /* last step: shortened to land on t_end, and the time set to t_end exactly */
+        double tn = t + dt;
+        if (tn >= t_end) {
+            dt = t_end - t;
+            tn = t_end;
+        }
         o_ssprk3_step(c, U, dt);
-        t += dt;
+        t = tn;
         ++steps;
     }
     if (t_out) *t_out = t;

@@ -1,0 +1,283 @@
+// k_sweep.cu -- the fused per-direction residual kernel of the WENO5-JS scheme.
+//
+// One launch handles one direction d of one stage.  A CTA owns a tile of W
+// grid lines along d, S cells each, and runs three phases through shared
+// memory:
+//   A. every stencil point of the tile (S + 6 per line: three ghost layers per
+//      side, Sec. 4.5) is loaded once, its ghost index mapped by the boundary
+//      rule, and its Lax-Friedrichs split flux f(+/-) (Sec. 2.2) computed once;
+//   B. every interface flux F^_{i+1/2} = WENO(+)(f+) + WENO(-)(f-) of the tile
+//      (S + 1 per line and component) is computed once, as one work item per
+//      (interface, component);
+//   C. every cell forms -(F^_{i+1/2} - F^_{i-1/2}) / h_d (Sec. 4.1) and the
+//      epilogue stores it, adds it to the accumulator of earlier directions,
+//      writes L(U), or -- for the last direction of a stage -- applies the
+//      SSP-RK3 stage combination (Eq. tt-ssprk3 without rounding) and
+//      publishes the wavespeed max of the new state for the next stage's alpha.
+//
+// FP64 mode computes everything in FP64.  FP32-bulk mode computes phases A-C
+// in FP32 on differences from a per-line reference state (exact to FP32
+// relative precision of the differences), and only the final state update
+// U^(k+1) = U^(k) + D is an FP64 add.
+#include <type_traits>
+
+#include "weno_dev.cuh"
+#include "weno_internal.h"
+
+namespace wg {
+
+constexpr int NT = 256;
+
+template <int DIR> struct Tile { static constexpr int W = 32, S = 26; };  // y, z: 32 x-lines, 26 cells
+template <> struct Tile<0> { static constexpr int W = 2, S = 122; };       // x: 2 rows, 122 cells
+
+constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int D, int DIR, bool BULK> struct Layout {
+    using T = typename std::conditional<BULK, float, double>::type;
+    static constexpr int NF = D + 2, W = Tile<DIR>::W, S = Tile<DIR>::S, NP = S + 6, NI = S + 1;
+    static constexpr size_t fp_off = 0;
+    static constexpr size_t fm_off = fp_off + sizeof(T) * NF * W * NP;
+    static constexpr size_t F_off = fm_off + sizeof(T) * NF * W * NP;
+    static constexpr size_t ref_off = align16(F_off + sizeof(T) * NF * W * NI);
+    static constexpr size_t bytes = ref_off + (BULK ? sizeof(RefState<D>) * W : 0);
+};
+
+template <int D, int DIR, bool BULK, int EPI>
+__global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
+{
+    using L = Layout<D, DIR, BULK>;
+    using T = typename L::T;
+    constexpr int NF = L::NF, W = L::W, S = L::S, NP = L::NP, NI = L::NI;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sfp = reinterpret_cast<T *>(smem + L::fp_off);
+    T *sfm = reinterpret_cast<T *>(smem + L::fm_off);
+    T *sF = reinterpret_cast<T *>(smem + L::F_off);
+    RefState<D> *sref = reinterpret_cast<RefState<D> *>(smem + L::ref_off);
+
+    const double dt = a.ctl->dt;
+    if (a.check_dt && dt == 0.0) return;  // the step is a no-op (time reached t_end)
+
+    const long long N = a.N;
+    const int n = a.n[DIR];
+    const long long st = a.stride[DIR];
+    int seg, lg, other;
+    if (DIR == 0) { seg = blockIdx.x; lg = blockIdx.y; other = blockIdx.z; }
+    else if (DIR == 1) { lg = blockIdx.x; seg = blockIdx.y; other = blockIdx.z; }
+    else { lg = blockIdx.x; other = blockIdx.y; seg = blockIdx.z; }
+    const int c0 = seg * S;
+    // Base offset of line w of the tile; false if the line lies outside the grid.
+    auto line = [&](int w, long long &base) -> bool {
+        if (DIR == 0) {
+            const int y = lg * W + w;
+            base = (long long)other * a.stride[2] + (long long)y * a.stride[1];
+            return y < a.n[1];
+        }
+        const int x = lg * W + w;
+        base = (long long)other * (DIR == 1 ? a.stride[2] : a.stride[1]) + x;
+        return x < a.n[0];
+    };
+
+    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    const double gm1 = a.gamma - 1.0;
+    const T eps = (T)a.eps;
+
+    // ---- phase 0 (FP32-bulk): reference state of every line
+    if (BULK) {
+        for (int w = threadIdx.x; w < W; w += NT) {
+            long long base;
+            const bool ok = line(w, base);
+            double q[NF];
+            const int cr = c0 < n ? c0 : n - 1;
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+                q[f] = ok ? a.U[f * N + base + (long long)cr * st] : (f == 0 || f == NF - 1 ? 1.0 : 0.0);
+            make_ref<D>(q, (float)gm1, sref[w]);
+        }
+        __syncthreads();
+    }
+
+    // ---- phase A: split point fluxes of the S + 6 stencil points of every line
+    for (int u = threadIdx.x; u < W * NP; u += NT) {
+        int w, p;
+        if (DIR == 0) { w = u / NP; p = u - w * NP; }
+        else { p = u / W; w = u - p * W; }
+        long long base;
+        T fpv[NF], fmv[NF];
+        if (line(w, base)) {
+            int c = c0 - 3 + p;
+            c = c < n + 2 ? c : n + 2;
+            bool flip;
+            const int cm = ghost_source(c, n, a.bc[DIR][0], a.bc[DIR][1], flip);
+            const double *src = a.U + base + (long long)cm * st;
+            double q[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = __ldg(src + f * N);
+            if (flip) q[1 + DIR] = -q[1 + DIR];
+            if constexpr (BULK) {
+                float dq[NF];
+                diff_from_ref<D>(q, sref[w], dq);
+                split_flux_diff<D, DIR>(dq, sref[w], (float)alpha, (float)gm1, fpv, fmv);
+            } else {
+                split_flux_f64<D, DIR>(q, alpha, gm1, fpv, fmv);
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) fpv[f] = fmv[f] = T(0);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            sfp[f * W * NP + u] = fpv[f];
+            sfm[f * W * NP + u] = fmv[f];
+        }
+    }
+    __syncthreads();
+
+    // ---- phase B: interface fluxes, one work item per (interface, component)
+    for (int u = threadIdx.x; u < NF * W * NI; u += NT) {
+        const int f = u / (W * NI);
+        const int r = u - f * (W * NI);
+        int w, j;
+        if (DIR == 0) { w = r / NI; j = r - w * NI; }
+        else { j = r / W; w = r - j * W; }
+        if (c0 + j - 1 >= n) continue;  // right of the last cell's right face
+        const T *P = sfp + f * W * NP;
+        const T *M = sfm + f * W * NP;
+        const int pw = DIR == 0 ? w * NP : w;
+        const int ps = DIR == 0 ? 1 : W;
+        // interface between local cells j-1 and j: f+ at points j..j+4, f- mirrored at j+5..j+1
+        const T Fh = weno5<T>(P[pw + j * ps], P[pw + (j + 1) * ps], P[pw + (j + 2) * ps], P[pw + (j + 3) * ps],
+                              P[pw + (j + 4) * ps], eps) +
+                     weno5<T>(M[pw + (j + 5) * ps], M[pw + (j + 4) * ps], M[pw + (j + 3) * ps],
+                              M[pw + (j + 2) * ps], M[pw + (j + 1) * ps], eps);
+        sF[f * W * NI + (DIR == 0 ? w * NI + j : j * W + w)] = Fh;
+    }
+    __syncthreads();
+
+    // ---- phase C: flux difference and epilogue
+    const T ih = (T)a.inv_h[DIR];
+    double cmax = 0.0;
+    float cmaxf = 0.0f;
+    bool bad = false;
+    // stage combination coefficients (Eq. tt-ssprk3): U' = a_n U^n + b_n (U^k + dt R)
+    const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
+    const double bn = a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0);
+    const float anf = (float)an;
+    const float bdtf = (float)(bn * dt);
+    for (int u = threadIdx.x; u < W * S; u += NT) {
+        int w, i;
+        if (DIR == 0) { w = u / S; i = u - w * S; }
+        else { i = u / W; w = u - i * W; }
+        long long base;
+        if (!line(w, base) || c0 + i >= n) continue;
+        const long long cell = base + (long long)(c0 + i) * st;
+        const int jl = DIR == 0 ? w * NI + i : i * W + w;
+        const int jr = DIR == 0 ? jl + 1 : jl + W;
+        T rd[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) rd[f] = -(sF[f * W * NI + jr] - sF[f * W * NI + jl]) * ih;
+        T *acc = reinterpret_cast<T *>(a.acc);
+        if (EPI == EPI_STORE) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f * N + cell] = rd[f];
+        } else if (EPI == EPI_ADD) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f * N + cell] += rd[f];
+        } else {
+            T r[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) r[f] = (D == 1) ? rd[f] : acc[f * N + cell] + rd[f];
+            if (EPI == EPI_RHS) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    if constexpr (BULK) a.Rout[f * N + cell] = f32_to_f64(r[f]);
+                    else a.Rout[f * N + cell] = r[f];
+                }
+            } else {  // EPI_STAGE
+                double out[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const double uk = a.U[f * N + cell];
+                    if constexpr (BULK) {
+                        float hk, lk;
+                        split_f64(uk, hk, lk);
+                        float dlt = bdtf * r[f];
+                        if (a.stage > 0) {
+                            float hn, ln;
+                            split_f64(a.Un[f * N + cell], hn, ln);
+                            dlt = fmaf(anf, (hn - hk) + (ln - lk), dlt);
+                        }
+                        out[f] = uk + f32_to_f64(dlt);
+                    } else {
+                        const double s = uk + dt * r[f];
+                        out[f] = a.stage == 0 ? s : an * a.Un[f * N + cell] + bn * s;
+                    }
+                    a.Uout[f * N + cell] = out[f];
+                }
+                bool b;
+                if constexpr (BULK) {
+                    float qf[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) qf[f] = f64_to_f32(out[f]);
+                    cmaxf = fmaxf(cmaxf, wavespeed_f32<D>(qf, (float)a.gamma, b));
+                } else {
+                    cmax = fmax(cmax, wavespeed_f64<D>(out, a.gamma, b));
+                }
+                bad |= b;
+            }
+        }
+    }
+    if (EPI == EPI_STAGE) {
+        if (BULK) cmax = (double)cmaxf;
+        block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+    }
+}
+
+static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+template <int D, int DIR, bool BULK, int EPI>
+static cudaError_t launch_t(const SweepArgs &a, cudaStream_t s)
+{
+    using L = Layout<D, DIR, BULK>;
+    dim3 grid;
+    if (DIR == 0) grid = dim3(cdiv(a.n[0], L::S), cdiv(a.n[1], L::W), (unsigned)a.n[2]);
+    else if (DIR == 1) grid = dim3(cdiv(a.n[0], L::W), cdiv(a.n[1], L::S), (unsigned)a.n[2]);
+    else grid = dim3(cdiv(a.n[0], L::W), (unsigned)a.n[1], cdiv(a.n[2], L::S));
+    k_sweep<D, DIR, BULK, EPI><<<grid, NT, L::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D, int DIR, bool BULK, int EPI>
+static cudaError_t attr_t()
+{
+    using L = Layout<D, DIR, BULK>;
+    return cudaFuncSetAttribute(k_sweep<D, DIR, BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)L::bytes);
+}
+
+#define WG_SWEEP_TABLE(X, B)                                                                              \
+    X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE) X(2, 0, B, EPI_STORE) X(2, 1, B, EPI_RHS) X(2, 1, B, EPI_STAGE) \
+        X(3, 0, B, EPI_STORE) X(3, 1, B, EPI_ADD) X(3, 2, B, EPI_RHS) X(3, 2, B, EPI_STAGE)
+
+cudaError_t sweep_set_attributes()
+{
+    cudaError_t e = cudaSuccess, r;
+#define X(D, DIR, B, E) \
+    if ((r = attr_t<D, DIR, B, E>()) != cudaSuccess) e = r;
+    WG_SWEEP_TABLE(X, false)
+    WG_SWEEP_TABLE(X, true)
+#undef X
+    return e;
+}
+
+cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
+{
+#define X(D, DIR, B, E) \
+    if (dim == D && dir == DIR && bulk == B && epi == E) return launch_t<D, DIR, B, E>(a, s);
+    WG_SWEEP_TABLE(X, false)
+    WG_SWEEP_TABLE(X, true)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace wg

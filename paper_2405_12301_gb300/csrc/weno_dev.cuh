@@ -1,0 +1,309 @@
+// weno_dev.cuh -- device building blocks of the GB300 WENO5-JS residual:
+// FP64 <-> FP32 conversions on the integer pipe, ghost-index mapping,
+// WENO5-JS reconstruction, point fluxes with Lax-Friedrichs splitting, and the
+// device control block.
+//
+// On GB300 the FP64 pipe (DFMA/DADD) and the FP32<->FP64 conversion
+// instructions both issue at about 1.7 per clock per SM, against about 86
+// FFMA per clock per SM, so the FP32-bulk path never converts with cvt and
+// keeps FP64 arithmetic to one DADD per field per stage.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wg {
+
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2 };
+
+// Device control block of one handle: time, step size and the stage alphas.
+// alpha[s] holds the bit pattern of a non-negative double so that atomicMax
+// on the 64-bit integer is a max on the value (order-independent, so the
+// result is bitwise deterministic).  Slot 0: alpha(U^n); slots 1..3: alpha of
+// the states written by stages 1..3.
+struct Ctl {
+    double t;              // current time
+    double t_next;         // time after the current step
+    double dt;             // dt of the current step (0: the step is a no-op)
+    double t_end;
+    double dt_req;         // > 0: fixed dt; otherwise CFL
+    double cfl_h;          // cfl * min_d h_d
+    unsigned long long alpha[4];
+    long long steps;       // steps taken since the last set_time
+    long long max_steps;   // steps bound of the current run call
+    int status;            // ST_* bits, latched
+    int pad;
+};
+
+// ----------------------------------------------------------------- conversions
+
+// Splits a finite FP64 x into FP32 hi + lo: hi is x truncated to 24 significant
+// bits, lo approximates x - hi (the next 23 bits).  Integer pipe plus one FSUB.
+// |x| below 2^-103 gives lo = 0; below 2^-126, hi = +-0; above FP32 range,
+// hi = +-inf (the callers flag such states as non-physical).
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo)
+{
+    const unsigned xh = (unsigned)__double2hiint(x);
+    const unsigned xl = (unsigned)__double2loint(x);
+    const unsigned e = (xh >> 20) & 0x7FFu;
+    const unsigned sgn = xh & 0x80000000u;
+    const unsigned hb = sgn | ((e - 896u) << 23) | ((xh & 0xFFFFFu) << 3) | (xl >> 29);
+    // lo = m29 * 2^(e-1075), m29 the low 29 mantissa bits: build 2^E (1 + (m29>>6)/2^23)
+    // with E = e - 1046 and subtract 2^E (exact).
+    const unsigned eb = (e - 919u) << 23;
+    const float fa = __uint_as_float(eb | ((xl & 0x1FFFFFFFu) >> 6));
+    const float fe = __uint_as_float(eb);
+    const float l = fa - fe;
+    const bool hi_ok = (e >= 897u) & (e <= 1150u);
+    hi = hi_ok ? __uint_as_float(hb) : __uint_as_float(e < 897u ? sgn : (sgn | 0x7F800000u));
+    lo = (hi_ok & (e >= 920u)) ? __uint_as_float(__float_as_uint(l) | sgn) : 0.0f;
+}
+
+// FP32 -> FP64, exact for normal numbers (subnormals flush to +-0).
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned sgn = b & 0x80000000u;
+    unsigned hi = sgn | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
+    unsigned lo = b << 29;
+    if (e == 0u) { hi = sgn; lo = 0u; }
+    if (e == 255u) { hi = sgn | 0x7FF00000u | ((b >> 3) & 0xFFFFFu); }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 -> FP32 by truncation (hi part of split_f64), integer pipe only.
+__device__ __forceinline__ float f64_to_f32(double x)
+{
+    float hi, lo;
+    split_f64(x, hi, lo);
+    return hi + lo;
+}
+
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ ghosts
+
+// Interior source index of a (possibly ghost) index c in [-3, n+2] along a
+// direction with n >= 3 cells (Sec. 4.5): periodic wraps, transmissive clamps,
+// reflective mirrors (and the caller negates the normal momentum).
+__device__ __forceinline__ int ghost_source(int c, int n, int bclo, int bchi, bool &flip)
+{
+    flip = false;
+    if (c < 0) {
+        if (bclo == BC_PERIODIC) return c + n;
+        if (bclo == BC_TRANSMISSIVE) return 0;
+        flip = true;
+        return -1 - c;
+    }
+    if (c >= n) {
+        if (bchi == BC_PERIODIC) return c - n;
+        if (bchi == BC_TRANSMISSIVE) return n - 1;
+        flip = true;
+        return 2 * n - 1 - c;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------- WENO5-JS
+
+template <typename T> __device__ __forceinline__ T div_(T a, T b);
+template <> __device__ __forceinline__ double div_<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float div_<float>(float a, float b) { return a * fast_rcp(b); }
+
+// Value at x_{i+1/2} reconstructed from (a, b, c, d, e) = v_{i-2}, ..., v_{i+2}
+// (Sec. 2.2): candidates v^(r), smoothness indicators beta_r, weights
+// alpha_r = d_r / (beta_r + eps)^2 normalised to sum one.  The normalisation is
+// folded into one division: with g_r = (beta_r + eps)^2,
+//   sum_r omega_r v^(r) = sum_r d_r g_s g_t (6 v^(r)) / (6 sum_r d_r g_s g_t),
+// {s, t} the other two indices, which is the same quantity.
+template <typename T>
+__device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps)
+{
+    const T k13 = T(13.0 / 12.0), q = T(0.25);
+    const T t0 = c - T(2) * d + e, s0 = T(3) * c - T(4) * d + e;
+    const T t1 = b - T(2) * c + d, s1 = b - d;
+    const T t2 = a - T(2) * b + c, s2 = a - T(4) * b + T(3) * c;
+    T g0 = k13 * t0 * t0 + q * s0 * s0 + eps;
+    T g1 = k13 * t1 * t1 + q * s1 * s1 + eps;
+    T g2 = k13 * t2 * t2 + q * s2 * s2 + eps;
+    g0 *= g0;
+    g1 *= g1;
+    g2 *= g2;
+    const T w0 = T(0.3) * (g1 * g2), w1 = T(0.6) * (g0 * g2), w2 = T(0.1) * (g0 * g1);
+    const T p0 = T(2) * c + T(5) * d - e;
+    const T p1 = -b + T(5) * c + T(2) * d;
+    const T p2 = T(2) * a - T(7) * b + T(11) * c;
+    return div_<T>(w0 * p0 + w1 * p1 + w2 * p2, T(6) * (w0 + w1 + w2));
+}
+
+// ----------------------------------------------------------- point fluxes
+
+// Plain FP64 Euler flux in direction DIR (Sec. 2.1) and its LF split
+// f(+/-) = (F +/- alpha U) / 2 (Sec. 2.2).
+template <int D, int DIR>
+__device__ __forceinline__ void split_flux_f64(const double *q, double alpha, double gm1, double *fp, double *fm)
+{
+    constexpr int NF = D + 2;
+    const double rho = q[0];
+    const double ir = 1.0 / rho;
+    double u[D];
+    double ke = 0.0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        u[e] = q[1 + e] * ir;
+        ke += u[e] * u[e];
+    }
+    const double p = gm1 * (q[D + 1] - 0.5 * rho * ke);
+    double F[NF];
+    F[0] = q[1 + DIR];
+#pragma unroll
+    for (int e = 0; e < D; ++e) F[1 + e] = q[1 + e] * u[DIR] + (e == DIR ? p : 0.0);
+    F[D + 1] = u[DIR] * (q[D + 1] + p);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        fp[f] = 0.5 * (F[f] + alpha * q[f]);
+        fm[f] = 0.5 * (F[f] - alpha * q[f]);
+    }
+}
+
+// Reference state of one tile line for the FP32-bulk path: the FP64 state
+// split into hi + lo, and FP32 primitives that only ever multiply differences.
+template <int D> struct RefState {
+    float hi[D + 2], lo[D + 2];
+    float rho, m[D], u[D], H;  // H = rho E + p
+};
+
+template <int D>
+__device__ __forceinline__ void make_ref(const double *q, float gm1, RefState<D> &r)
+{
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) split_f64(q[f], r.hi[f], r.lo[f]);
+    r.rho = r.hi[0];
+    const float ir = 1.0f / r.rho;
+    float ke = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        r.m[e] = r.hi[1 + e];
+        r.u[e] = r.m[e] * ir;
+        ke += r.m[e] * r.u[e];
+    }
+    const float p = gm1 * (r.hi[D + 1] - 0.5f * ke);
+    r.H = r.hi[D + 1] + p;
+}
+
+// dq = q - ref, formed from the hi/lo splits so that it carries the full FP32
+// relative precision of the difference (not of q).
+template <int D>
+__device__ __forceinline__ void diff_from_ref(const double *q, const RefState<D> &r, float *dq)
+{
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) {
+        float hi, lo;
+        split_f64(q[f], hi, lo);
+        dq[f] = (hi - r.hi[f]) + (lo - r.lo[f]);
+    }
+}
+
+// Split-flux differences df(+/-) = f(+/-)(ref + dq) - f(+/-)(ref) in FP32,
+// using only exact product-difference identities
+//   d(ab) = da * b + a_ref * db,  du = (dm - u_ref drho) / rho,
+// so every rounding error is relative to the differences, not to the state.
+template <int D, int DIR>
+__device__ __forceinline__ void split_flux_diff(const float *dq, const RefState<D> &r, float alpha, float gm1,
+                                                float *fp, float *fm)
+{
+    constexpr int NF = D + 2;
+    const float rho = r.rho + dq[0];
+    const float ir = fast_rcp(rho);
+    float du[D], u[D];
+    float dk = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        du[e] = (dq[1 + e] - r.u[e] * dq[0]) * ir;
+        u[e] = r.u[e] + du[e];
+        dk += dq[1 + e] * u[e] + r.m[e] * du[e];
+    }
+    const float dp = gm1 * (dq[D + 1] - 0.5f * dk);
+    float dF[NF];
+    dF[0] = dq[1 + DIR];
+#pragma unroll
+    for (int e = 0; e < D; ++e) dF[1 + e] = dq[1 + e] * u[DIR] + r.m[e] * du[DIR] + (e == DIR ? dp : 0.0f);
+    const float dH = dq[D + 1] + dp;
+    dF[D + 1] = du[DIR] * (r.H + dH) + r.u[DIR] * dH;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        fp[f] = 0.5f * (dF[f] + alpha * dq[f]);
+        fm[f] = 0.5f * (dF[f] - alpha * dq[f]);
+    }
+}
+
+// ------------------------------------------------------------- wavespeed
+
+// |u| + sqrt(gamma p / rho) in FP64 with the operation order of the plain
+// formula (no contraction), so that alpha and dt reproduce it bit for bit.
+template <int D>
+__device__ __forceinline__ double wavespeed_f64(const double *q, double gamma, bool &bad)
+{
+    const double rho = q[0];
+    double u2 = 0.0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const double ue = __ddiv_rn(q[1 + e], rho);
+        u2 = __dadd_rn(u2, __dmul_rn(ue, ue));
+    }
+    const double p = __dmul_rn(gamma - 1.0, __dsub_rn(q[D + 1], __dmul_rn(__dmul_rn(0.5, rho), u2)));
+    bad = !(rho > 0.0) || !(p > 0.0) || !isfinite(u2) || !isfinite(q[D + 1]);
+    const double a = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+    return bad ? 0.0 : __dadd_rn(__dsqrt_rn(u2), a);
+}
+
+template <int D>
+__device__ __forceinline__ float wavespeed_f32(const float *q, float gamma, bool &bad)
+{
+    const float rho = q[0];
+    const float ir = 1.0f / rho;
+    float u2 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const float ue = q[1 + e] * ir;
+        u2 += ue * ue;
+    }
+    const float p = (gamma - 1.0f) * (q[D + 1] - 0.5f * rho * u2);
+    bad = !(rho > 0.0f) || !(p > 0.0f) || !isfinite(u2) || !isfinite(q[D + 1]);
+    return bad ? 0.0f : sqrtf(u2) + sqrtf(gamma * p * ir);
+}
+
+// Block-wide max of a non-negative value, then one atomicMax per block on the
+// 64-bit pattern of the double.  Also ORs the block's non-physical flag into
+// the status word.  Every thread of the block must call it.
+__device__ __forceinline__ void block_max_publish(double v, bool bad, unsigned long long *slot, int *status)
+{
+    __shared__ double warp_max[32];
+    __shared__ int any_bad;
+    if (threadIdx.x == 0) any_bad = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    __syncthreads();
+    if (bad) any_bad = 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_max[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double m = lane < nw ? warp_max[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if (lane == 0) {
+            if (m > 0.0) atomicMax(slot, (unsigned long long)__double_as_longlong(m));
+            if (any_bad) atomicOr(status, ST_NONPHYSICAL);
+        }
+    }
+}
+
+}  // namespace wg

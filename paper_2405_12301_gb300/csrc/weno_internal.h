@@ -1,0 +1,79 @@
+// weno_internal.h -- interface between the C ABI layer and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wg {
+
+struct Ctl;
+
+// Epilogue of a sweep kernel (what it does with the direction's residual).
+enum Epi { EPI_STORE = 0, EPI_ADD = 1, EPI_RHS = 2, EPI_STAGE = 3 };
+
+struct SweepArgs {
+    const double *U;     // stencil state U^(k) (device, FP64 SoA)
+    const double *Un;    // U^n, read by the stage-2/3 combination
+    double *Uout;        // U^(k+1)
+    void *acc;           // residual accumulator: float (FP32-bulk) or double (FP64)
+    double *Rout;        // output of EPI_RHS
+    Ctl *ctl;
+    long long N;         // cells per field (field stride)
+    int n[3];
+    long long stride[3]; // 1, nx, nx * ny
+    int bc[3][2];
+    double inv_h[3];
+    double gamma;
+    double eps;
+    int stage;           // 0, 1, 2
+    int slot_in;         // alpha slot used for the splitting
+    int slot_out;        // alpha slot the EPI_STAGE epilogue publishes to
+    int check_dt;        // skip all work when ctl->dt == 0
+};
+
+// Launches the sweep of direction dir for a dim-dimensional grid.
+cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
+cudaError_t sweep_set_attributes();
+
+cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
+                         cudaStream_t s);
+cudaError_t launch_reset_slot(Ctl *ctl, int slot, cudaStream_t s);
+cudaError_t launch_step_begin(Ctl *ctl, cudaStream_t s);
+cudaError_t launch_step_end(Ctl *ctl, cudaStream_t s);
+cudaError_t launch_copy_alpha(const Ctl *ctl, int slot, double *out, cudaStream_t s);
+cudaError_t launch_sums(const double *U, int nf, long long N, double *partials, int nblocks, double *out,
+                        cudaStream_t s);
+int sums_blocks(long long N);
+
+// ---------------------------------------------------------------- cross eval
+struct CrossInst {
+    int n[3];
+    int r[2];
+    const float *core[5][3];
+    double h[3];
+    double alpha;
+    int bc[3][2];
+};
+
+struct CrossSet {
+    int inst, mode, fd;
+    int n_mode;
+    long long n_left, n_right;
+    const int *left;
+    const int *right;
+    void *out;
+    long long work_begin;  // first work item of this set (prefix sum)
+};
+
+struct CrossArgs {
+    const CrossInst *inst;
+    const CrossSet *sets;
+    int n_sets;
+    long long n_work;      // total work items
+    double gamma, eps;
+    unsigned long long *counter;
+    int fp64;
+};
+
+cudaError_t launch_cross(const CrossArgs &a, cudaStream_t s);
+
+}  // namespace wg

@@ -1,0 +1,289 @@
+"""ctypes binding of the GB300 WENO5-JS library (include/weno_gb300.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``_lib/libweno_gb300.so``.  Device arrays are torch tensors (FP64,
+contiguous, on the current CUDA device); the binding passes their data
+pointers and torch's current stream.  There is no CPU fallback: if the library
+is missing or a call fails, an exception is raised.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libweno_gb300.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+FP64, FP32_BULK = 0, 1
+ALPHA_GLOBAL_NORM, ALPHA_PER_DIR = 0, 1
+CROSS_FP64_CHECK = 1
+
+EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
+           "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
+           "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read")
+PROFILE_KINDS = 8
+
+
+class WenoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("weno status %d: %s" % (code, msg))
+        self.code = code
+
+
+class weno_grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("reserved", C.c_int32), ("n", C.c_int64 * 3),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class weno_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("eps_weno", C.c_double), ("cfl", C.c_double),
+                ("bc", (C.c_int32 * 2) * 3), ("precision", C.c_int32), ("alpha_mode", C.c_int32)]
+
+
+class weno_tt_instance(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("r", C.c_int32 * 2), ("reserved", C.c_int32),
+                ("core", (C.c_void_p * 3) * 5), ("h", C.c_double * 3), ("alpha", C.c_double),
+                ("bc", (C.c_int32 * 2) * 3)]
+
+
+class weno_fiber_set(C.Structure):
+    _fields_ = [("instance", C.c_int32), ("mode", C.c_int32), ("flux_dir", C.c_int32), ("reserved", C.c_int32),
+                ("n_left", C.c_int64), ("n_right", C.c_int64), ("left", C.c_void_p), ("right", C.c_void_p),
+                ("out", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libweno_gb300.so is missing; run __graft_entry__.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        P, d, i64, i32, vp = C.POINTER, C.c_double, C.c_int64, C.c_int32, C.c_void_p
+        L.weno_init.argtypes = [P(vp), P(weno_grid), P(weno_params), vp]
+        L.weno_destroy.argtypes = [vp]
+        L.weno_set_stream.argtypes = [vp, vp]
+        L.weno_alpha.argtypes = [vp, vp, vp]
+        L.weno_rhs.argtypes = [vp, vp, vp, vp]
+        L.weno_set_time.argtypes = [vp, d]
+        L.weno_get_time.argtypes = [vp, P(d), P(i64)]
+        L.weno_ssprk3_step.argtypes = [vp, vp, d, d]
+        L.weno_run.argtypes = [vp, vp, d, d, i64, i32, P(i64)]
+        L.weno_run_host.argtypes = [vp, vp, d, d, i64, i32, P(i64)]
+        L.weno_sums.argtypes = [vp, vp, vp]
+        L.weno_sync.argtypes = [vp]
+        L.weno_last_error.argtypes = [vp]
+        L.weno_last_error.restype = C.c_char_p
+        L.weno_cross_eval.argtypes = [vp, P(weno_tt_instance), i32, P(weno_fiber_set), i32, i32]
+        L.weno_profile_enable.argtypes = [vp, i32]
+        L.weno_profile_read.argtypes = [vp, P(d), P(i64), P(i64)]
+        for name in EXPORTS:
+            if name != "weno_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(h, code):
+    if code != OK:
+        msg = lib().weno_last_error(h)
+        raise WenoError(code, msg.decode() if msg else "")
+    return code
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------ thin wrappers
+def weno_init(dim=None, n=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=1.4, eps_weno=1e-6, cfl=0.5,
+              bc=((BC_PERIODIC, BC_PERIODIC),) * 3, precision=FP64, alpha_mode=ALPHA_GLOBAL_NORM, stream=None):
+    """Returns a handle (c_void_p).  dim=None makes a cross-eval-only handle."""
+    g = None
+    if dim is not None:
+        g = weno_grid()
+        g.dim = dim
+        nn = list(n) + [1] * (3 - len(n))
+        for k in range(3):
+            g.n[k] = int(nn[k])
+            g.lo[k] = float(lo[k]) if k < len(lo) else 0.0
+            g.hi[k] = float(hi[k]) if k < len(hi) else 1.0
+    p = weno_params()
+    p.gamma, p.eps_weno, p.cfl = gamma, eps_weno, cfl
+    for k in range(3):
+        p.bc[k][0], p.bc[k][1] = bc[k] if k < len(bc) else (BC_PERIODIC, BC_PERIODIC)
+    p.precision, p.alpha_mode = precision, alpha_mode
+    h = C.c_void_p()
+    code = lib().weno_init(C.byref(h), C.byref(g) if g is not None else None, C.byref(p),
+                           stream if stream is not None else _stream())
+    if code != OK:
+        raise WenoError(code, lib().weno_last_error(None).decode())
+    return h
+
+
+def weno_destroy(h):
+    return _check(h, lib().weno_destroy(h))
+
+
+def weno_alpha(h, U, alpha_out):
+    import torch
+    return _check(h, lib().weno_alpha(h, _ptr(U, torch.float64), _ptr(alpha_out, torch.float64)))
+
+
+def weno_rhs(h, U, R, alpha_out=None):
+    import torch
+    a = _ptr(alpha_out, torch.float64) if alpha_out is not None else None
+    return _check(h, lib().weno_rhs(h, _ptr(U, torch.float64), _ptr(R, torch.float64), a))
+
+
+def weno_set_time(h, t):
+    return _check(h, lib().weno_set_time(h, float(t)))
+
+
+def weno_get_time(h):
+    t, s = C.c_double(), C.c_int64()
+    _check(h, lib().weno_get_time(h, C.byref(t), C.byref(s)))
+    return t.value, s.value
+
+
+def weno_ssprk3_step(h, U, t_end, dt=0.0):
+    import torch
+    return _check(h, lib().weno_ssprk3_step(h, _ptr(U, torch.float64), float(t_end), float(dt)))
+
+
+def weno_run(h, U, t_end, dt=0.0, max_steps=1 << 62, graph_steps=16):
+    import torch
+    s = C.c_int64()
+    _check(h, lib().weno_run(h, _ptr(U, torch.float64), float(t_end), float(dt), int(max_steps),
+                             int(graph_steps), C.byref(s)))
+    return s.value
+
+
+def weno_run_host(h, U_host, t_end, dt=0.0, max_steps=1 << 62, graph_steps=16):
+    """U_host: a contiguous FP64 CPU tensor (pinned is fastest), updated in place."""
+    import torch
+    if U_host.is_cuda or not U_host.is_contiguous() or U_host.dtype != torch.float64:
+        raise ValueError("expected a contiguous FP64 CPU tensor")
+    s = C.c_int64()
+    _check(h, lib().weno_run_host(h, C.c_void_p(U_host.data_ptr()), float(t_end), float(dt), int(max_steps),
+                                  int(graph_steps), C.byref(s)))
+    return s.value
+
+
+def weno_sums(h, U, nf):
+    import torch
+    out = (C.c_double * nf)()
+    _check(h, lib().weno_sums(h, _ptr(U, torch.float64), out))
+    return list(out)
+
+
+def weno_sync(h):
+    return _check(h, lib().weno_sync(h))
+
+
+def weno_profile_enable(h, enable=True):
+    return _check(h, lib().weno_profile_enable(h, 1 if enable else 0))
+
+
+def weno_profile_read(h):
+    """(ms per kind, launches per kind, total kernel launches) since the last enable."""
+    ms = (C.c_double * PROFILE_KINDS)()
+    n = (C.c_int64 * PROFILE_KINDS)()
+    tot = C.c_int64()
+    _check(h, lib().weno_profile_read(h, ms, n, C.byref(tot)))
+    return list(ms), list(n), tot.value
+
+
+def weno_cross_eval(h, instances, sets, fp64_check=False):
+    """instances: list of dict(n, r, cores=[5][3] CUDA float32 tensors, h, alpha, bc);
+    sets: list of dict(instance, mode, flux_dir, left, right, out) with CUDA tensors."""
+    import torch
+    inst = (weno_tt_instance * len(instances))()
+    for k, d in enumerate(instances):
+        for m in range(3):
+            inst[k].n[m] = int(d["n"][m])
+            inst[k].h[m] = float(d["h"][m])
+            inst[k].bc[m][0], inst[k].bc[m][1] = d["bc"][m]
+        for m in range(2):
+            inst[k].r[m] = int(d["r"][m])
+        for f in range(5):
+            for m in range(3):
+                inst[k].core[f][m] = _ptr(d["cores"][f][m], torch.float32).value
+        inst[k].alpha = float(d["alpha"])
+    fs = (weno_fiber_set * len(sets))()
+    for k, s in enumerate(sets):
+        fs[k].instance, fs[k].mode, fs[k].flux_dir = s["instance"], s["mode"], s["flux_dir"]
+        fs[k].n_left = s["left"].shape[0] if s["left"] is not None else 1
+        fs[k].n_right = s["right"].shape[0] if s["right"] is not None else 1
+        fs[k].left = _ptr(s["left"], torch.int32).value if s["left"] is not None else None
+        fs[k].right = _ptr(s["right"], torch.int32).value if s["right"] is not None else None
+        fs[k].out = _ptr(s["out"], torch.float64 if fp64_check else torch.float32).value
+    return _check(h, lib().weno_cross_eval(h, inst, len(instances), fs, len(sets),
+                                           CROSS_FP64_CHECK if fp64_check else 0))
+
+
+class Solver:
+    """Owns one handle: a grid, its parameters and its scratch."""
+
+    def __init__(self, dim, n, lo=None, hi=None, **kw):
+        lo = lo if lo is not None else (0.0,) * dim
+        hi = hi if hi is not None else (1.0,) * dim
+        self.dim, self.n, self.nf = dim, tuple(n), dim + 2
+        self.h = weno_init(dim, n, lo, hi, **kw)
+
+    def close(self):
+        if self.h is not None:
+            weno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rhs(self, U, R, alpha_out=None):
+        return weno_rhs(self.h, U, R, alpha_out)
+
+    def alpha(self, U, out):
+        return weno_alpha(self.h, U, out)
+
+    def set_time(self, t):
+        return weno_set_time(self.h, t)
+
+    def time(self):
+        return weno_get_time(self.h)
+
+    def step(self, U, t_end=float("inf"), dt=0.0):
+        return weno_ssprk3_step(self.h, U, t_end, dt)
+
+    def run(self, U, t_end, dt=0.0, max_steps=1 << 62, graph_steps=16):
+        return weno_run(self.h, U, t_end, dt, max_steps, graph_steps)
+
+    def run_host(self, U_host, t_end, dt=0.0, max_steps=1 << 62, graph_steps=16):
+        return weno_run_host(self.h, U_host, t_end, dt, max_steps, graph_steps)
+
+    def sums(self, U):
+        return weno_sums(self.h, U, self.nf)
+
+    def sync(self):
+        return weno_sync(self.h)
+
+    def profile_enable(self, enable=True):
+        return weno_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        return weno_profile_read(self.h)

@@ -1,0 +1,369 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  GPU only.
+
+Tolerances (derivations in the design notes):
+  * FP64 residual: |a - b| <= 1e-12 max(|b|, |b_f|_inf) + 1e-13 S_f / h, where
+    S_f = alpha |U_f|_inf + |rho E|_inf bounds the split fluxes of field f: the
+    GPU forms the same WENO sums with a different (equivalent) expression tree,
+    so each interface flux may differ by a few ulp of S_f, and the flux
+    difference divides that by h.
+  * FP64 state after one step: 1e-12 relative per cell; after a run: 1e-10
+    (field scale max(|b|, |b_f|_inf)).
+  * FP32-bulk residual: 32 * 2^-24 * V_f / h + 1e-6 |R_f|_inf, V_f the largest
+    variation of the split fluxes along a line (the bulk path rounds
+    differences from a per-line reference, so its error scales with the
+    variation, not with the magnitude, of the data).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2405_12301_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P, T, R = O.PERIODIC, O.TRANSMISSIVE, O.REFLECTIVE
+
+
+@pytest.fixture(scope="module")
+def W():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_12301_gb300 import build, weno
+    build.build()
+    weno.lib()
+    return weno
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def solver(W, cfg, precision=0, cfl=0.5):
+    return W.Solver(cfg.dim, cfg.n[:cfg.dim], cfg.lo[:cfg.dim], cfg.hi[:cfg.dim], gamma=cfg.gamma,
+                    eps_weno=cfg.eps, cfl=cfl, bc=cfg.bc, precision=precision)
+
+
+def fp64_rhs_tol(cfg, U, Rref, alpha):
+    nf = U.shape[0]
+    hmin = min(cfg.spacing(d) for d in range(cfg.dim))
+    tol = np.empty_like(Rref)
+    for f in range(nf):
+        S = alpha * np.abs(U[f]).max() + np.abs(U[-1]).max()
+        tol[f] = 1e-12 * np.maximum(np.abs(Rref[f]), np.abs(Rref[f]).max()) + 1e-13 * S / hmin
+    return tol
+
+
+def rel_field_err(a, b):
+    err = 0.0
+    for f in range(b.shape[0]):
+        scale = np.maximum(np.abs(b[f]), np.abs(b[f]).max())
+        err = max(err, float((np.abs(a[f] - b[f]) / scale).max()))
+    return err
+
+
+CASES = [
+    (1, (300,), ((P, P),)),
+    (1, (257,), ((T, R),)),
+    (2, (130, 60), ((P, P), (P, P))),
+    (2, (123, 27), ((T, T), (R, T))),
+    (2, (64, 52), ((R, R), (T, P))),
+    (3, (45, 30, 29), ((P, P), (P, P), (P, P))),
+    (3, (26, 27, 33), ((T, R), (P, T), (R, R))),
+]
+
+
+@pytest.mark.parametrize("dim,n,bc", CASES)
+def test_rhs_fp64_matches_oracle(W, dim, n, bc):
+    cfg = O.Cfg(dim=dim, n=n, bc=bc)
+    U = I.random_state(dim, n, seed=100 + sum(n), jumps=True)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg)
+    Ud, Rd, ad = dev(U), torch.empty(U.shape, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.float64,
+                                                                                                 device="cuda")
+    s.rhs(Ud, Rd, ad)
+    Rg = host(Rd)
+    assert host(ad)[0] == aref[0], "alpha must be bitwise equal"
+    tol = fp64_rhs_tol(cfg, U, Rref, aref[0])
+    bad = np.abs(Rg - Rref) > tol
+    assert not bad.any(), (np.abs(Rg - Rref)[bad].max(), np.argwhere(bad)[:5])
+
+
+@pytest.mark.parametrize("n", [(3,), (122,), (244,)])
+def test_rhs_fp64_edge_sizes_1d(W, n):
+    """Smallest grid (3 cells: every ghost wraps onto the interior) and exact tile multiples."""
+    for bc in ((P, P), (T, T), (R, R)):
+        cfg = O.Cfg(dim=1, n=n, bc=(bc,))
+        U = I.random_state(1, n, seed=7, jumps=True)
+        Rref, aref = O.residual(cfg, U)
+        s = solver(W, cfg)
+        Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+        s.rhs(dev(U), Rd)
+        assert (np.abs(host(Rd) - Rref) <= fp64_rhs_tol(cfg, U, Rref, aref[0])).all()
+
+
+def test_rhs_fp64_edge_sizes_3d(W):
+    for n in ((3, 3, 3), (32, 26, 26), (4, 52, 3)):
+        cfg = O.Cfg(dim=3, n=n)
+        U = I.random_state(3, n, seed=9, jumps=True)
+        Rref, aref = O.residual(cfg, U)
+        s = solver(W, cfg)
+        Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+        s.rhs(dev(U), Rd)
+        assert (np.abs(host(Rd) - Rref) <= fp64_rhs_tol(cfg, U, Rref, aref[0])).all(), n
+
+
+@pytest.mark.parametrize("dim,n,bc", CASES)
+def test_step_fp64_matches_oracle(W, dim, n, bc):
+    """One SSP-RK3 step with the CFL dt: <= 1e-12 relative per cell."""
+    cfg = O.Cfg(dim=dim, n=n, bc=bc)
+    U = I.random_state(dim, n, seed=200 + sum(n), jumps=True)
+    dt = O.cfl_dt(cfg, U, 0.5)
+    Uref = O.ssprk3_step(cfg, U, dt)
+    s = solver(W, cfg)
+    Ud = dev(U)
+    s.set_time(0.0)
+    s.step(Ud, t_end=1e9)
+    t, steps = s.time()
+    assert steps == 1 and t == dt
+    assert rel_field_err(host(Ud), Uref) <= 1e-12
+
+
+def test_run_fp64_matches_oracle(W):
+    """Whole runs agree to <= 1e-10 relative: 1D wave, 2D quadrant problem, 3D wave."""
+    runs = [
+        (O.Cfg(dim=1, n=(64,), lo=(0.0,), hi=(2.0,)), I.density_wave(1, (64,)), 0.5),
+        (O.Cfg(dim=2, n=(48, 48), bc=((T, T), (T, T))), I.quadrant_riemann((48, 48)), 0.08),
+        (O.Cfg(dim=3, n=(16, 12, 10), lo=(0, 0, 0), hi=(2.0, 1.5, 1.25)),
+         I.random_state(3, (16, 12, 10), seed=3), 0.05),
+    ]
+    for cfg, U0, t_end in runs:
+        Uref, steps, t = O.run(cfg, U0, t_end, cfl=0.5)
+        s = solver(W, cfg)
+        Ud = dev(U0)
+        s.set_time(0.0)
+        gsteps = s.run(Ud, t_end, graph_steps=8)
+        tg, _ = s.time()
+        assert gsteps == steps and tg == t_end
+        assert rel_field_err(host(Ud), Uref) <= 1e-10, cfg.dim
+
+
+def test_graph_run_equals_plain_steps_bitwise(W):
+    cfg = O.Cfg(dim=2, n=(70, 40))
+    U0 = I.random_state(2, (70, 40), seed=12, jumps=True)
+    a, b, c = dev(U0), dev(U0), dev(U0)
+    for Ud, mode in ((a, "graph"), (b, "plain"), (c, "step")):
+        s = solver(W, cfg)
+        s.set_time(0.0)
+        if mode == "graph":
+            assert s.run(Ud, 1e9, max_steps=10, graph_steps=4) == 10
+        elif mode == "plain":
+            assert s.run(Ud, 1e9, max_steps=10, graph_steps=0) == 10
+        else:
+            for _ in range(10):
+                s.step(Ud, 1e9)
+    # run() carries alpha between steps, step() recomputes it: the same value either way
+    assert torch.equal(a, b) and torch.equal(a, c)
+
+
+def test_run_host_equals_device_run(W):
+    cfg = O.Cfg(dim=2, n=(40, 36))
+    U0 = I.random_state(2, (40, 36), seed=13)
+    s = solver(W, cfg)
+    Ud = dev(U0)
+    s.set_time(0.0)
+    s.run(Ud, 1e9, max_steps=5)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    s2 = solver(W, cfg)
+    s2.set_time(0.0)
+    assert s2.run_host(Uh, 1e9, max_steps=5) == 5
+    assert torch.equal(Uh, Ud.cpu())
+
+
+def test_sums_fixed_order_and_match_oracle(W):
+    cfg = O.Cfg(dim=3, n=(40, 30, 20))
+    U = I.random_state(3, (40, 30, 20), seed=14, jumps=True)
+    s = solver(W, cfg)
+    Ud = dev(U)
+    a, b = s.sums(Ud), s.sums(Ud)
+    assert a == b
+    ref = O.sums(cfg, U)
+    scale = np.abs(U).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(np.array(a) - ref) <= 1e-14 * scale)
+
+
+def test_periodic_fp64_run_conserves(W):
+    cfg = O.Cfg(dim=2, n=(96, 80))
+    U0 = I.random_state(2, (96, 80), seed=15, jumps=True)
+    s = solver(W, cfg)
+    Ud = dev(U0)
+    s0 = np.array(s.sums(Ud))
+    s.set_time(0.0)
+    s.run(Ud, 1e9, max_steps=50)
+    s1 = np.array(s.sums(Ud))
+    scale = np.abs(U0).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(s1 - s0) <= 1e-13 * scale), (s1 - s0) / scale
+
+
+def test_nonphysical_state_is_reported_not_faulted(W):
+    """A negative-pressure cell made on the host is flagged by the kernels'
+    own checks and reported as WENO_ERR_NONPHYSICAL; the context stays usable."""
+    cfg = O.Cfg(dim=2, n=(32, 32))
+    U = I.random_state(2, (32, 32), seed=16)
+    U[3, 0, 5, 7] = -1.0  # rho E < 0 -> p < 0
+    s = solver(W, cfg)
+    a = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.alpha(dev(U), a)
+    with pytest.raises(W.WenoError) as e:
+        s.sync()
+    assert e.value.code == W.ERR_NONPHYSICAL
+    s.sync()  # cleared after being reported
+    U2 = I.random_state(2, (32, 32), seed=16)
+    s.alpha(dev(U2), a)
+    s.sync()
+    assert host(a)[0] == O.alpha_max(cfg, U2)
+
+
+# ------------------------------------------------------------- FP32-bulk path
+def _variation_tol(cfg, U, Rref, alpha):
+    """32 * 2^-24 * V_f / h + 1e-6 |R_f|_inf with V_f = (1 + alpha) * max line variation of
+    (U_f, rho E), an upper bound of the variation of the split fluxes along a line."""
+    nf = U.shape[0]
+    hmin = min(cfg.spacing(d) for d in range(cfg.dim))
+    tol = np.empty_like(Rref)
+    for f in range(nf):
+        v = 0.0
+        for d in range(cfg.dim):
+            ax = 3 - d
+            for g in (f, nf - 1, 0):
+                v = max(v, float((U[g].max(axis=ax - 1) - U[g].min(axis=ax - 1)).max()))
+        V = (1.0 + alpha) * v * (1.0 + np.abs(U[1:nf - 1]).max() / np.abs(U[0]).min())
+        tol[f] = 32 * 2.0 ** -24 * V / hmin + 1e-6 * np.abs(Rref[f]).max()
+    return tol
+
+
+@pytest.mark.parametrize("dim,n,bc", CASES)
+def test_rhs_bulk_matches_oracle(W, dim, n, bc):
+    cfg = O.Cfg(dim=dim, n=n, bc=bc)
+    U = I.random_state(dim, n, seed=300 + sum(n), jumps=True)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg, precision=1)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    Rg = host(Rd)
+    tol = _variation_tol(cfg, U, Rref, aref[0])
+    assert (np.abs(Rg - Rref) <= tol).all(), float((np.abs(Rg - Rref) / tol).max())
+
+
+def test_bulk_error_scales_with_variation_not_magnitude(W):
+    """rho = 1000 + 0.2 sin: plain FP32 would lose the wave in rounding
+    (2^-24 * 1000 / h ~ 1e-2 in R); differences from a line reference keep R
+    accurate to the variation's precision."""
+    n = (256,)
+    cfg = O.Cfg(dim=1, n=n, lo=(0.0,), hi=(2.0,))
+    U = I.density_wave(1, n)
+    rho = U[0] + 999.0
+    U = I.conserved(1, rho, [np.ones_like(rho)], np.full_like(rho, 1000.0))
+    Rref, a = O.residual(cfg, U)
+    s = solver(W, cfg, precision=1)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    err = np.abs(host(Rd)[0] - Rref[0]).max()
+    plain = 2.0 ** -24 * np.abs(U[0]).max() * a[0] / cfg.spacing(0)
+    assert err < 1e-3 * plain, (err, plain)
+    assert (np.abs(host(Rd) - Rref) <= _variation_tol(cfg, U, Rref, a[0])).all()
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_bulk_l1_within_1p1_of_fp64_above_floor(W, N):
+    """2D density wave to t = 2: the FP32-bulk L1 error against the exact
+    solution is within 1.1x of the FP64 run wherever the FP64 error is at least
+    10x the FP32 floor (the L1 difference of the two GPU runs)."""
+    cfg = O.Cfg(dim=2, n=(N, N), lo=(0.0, 0.0), hi=(2.0, 2.0))
+    U0 = I.density_wave(2, (N, N))
+    ex = I.density_wave(2, (N, N), t=2.0)
+    out = {}
+    for prec in (0, 1):
+        s = solver(W, cfg, precision=prec)
+        Ud = dev(U0)
+        s.set_time(0.0)
+        s.run(Ud, 2.0, graph_steps=16)
+        out[prec] = host(Ud)
+    e64 = np.abs(out[0][0] - ex[0]).mean()
+    e32 = np.abs(out[1][0] - ex[0]).mean()
+    floor = np.abs(out[1][0] - out[0][0]).mean()
+    print("N=%d e64=%.3e e32=%.3e floor=%.3e" % (N, e64, e32, floor))
+    assert e64 >= 10 * floor, (e64, floor)
+    assert e32 <= 1.1 * e64
+
+
+def test_bulk_periodic_conservation_drift_is_small(W):
+    cfg = O.Cfg(dim=2, n=(128, 96))
+    U0 = I.random_state(2, (128, 96), seed=17, jumps=True)
+    s = solver(W, cfg, precision=1)
+    Ud = dev(U0)
+    s0 = np.array(s.sums(Ud))
+    s.set_time(0.0)
+    s.run(Ud, 1e9, max_steps=50)
+    s1 = np.array(s.sums(Ud))
+    scale = np.abs(U0).sum(axis=(1, 2, 3))
+    drift = np.abs(s1 - s0) / scale
+    print("bulk conservation drift after 50 steps:", drift)
+    assert np.all(drift <= 1e-9)
+
+
+# ----------------------------------------------------- full-size workloads
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_2d_rhs(W, precision):
+    """2048^2, the benchmark's 2D grid and launch configuration: every residual
+    value against the oracle (random state with jumps)."""
+    n = (2048, 2048)
+    cfg = O.Cfg(dim=2, n=n, lo=(0.0, 0.0), hi=(2.0, 2.0))
+    U = I.random_state(2, n, seed=18, jumps=True, length=2.0)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg, precision=precision)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    Rg = host(Rd)
+    tol = fp64_rhs_tol(cfg, U, Rref, aref[0]) if precision == 0 else _variation_tol(cfg, U, Rref, aref[0])
+    assert (np.abs(Rg - Rref) <= tol).all()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_3d_x_only_field_matches_1d_oracle(W, precision):
+    """256^3 (the 3D benchmark grid): a state that varies along x only has zero y
+    and z flux differences, so every x-line of the 3D residual equals the 1D
+    oracle residual of that line (with the 3D alpha)."""
+    N = 256
+    cfg3 = O.Cfg(dim=3, n=(N, N, N), lo=(0, 0, 0), hi=(2.0, 2.0, 2.0))
+    U1 = I.random_state(1, (N,), seed=19, jumps=True, length=2.0)  # rho, rho u, E
+    U3 = np.zeros((5, N, N, N))
+    U3[0] = U1[0, 0, 0][None, None, :]
+    U3[1] = U1[1, 0, 0][None, None, :]
+    U3[4] = U1[2, 0, 0][None, None, :]
+    s = solver(W, cfg3, precision=precision)
+    Rd = torch.empty(U3.shape, dtype=torch.float64, device="cuda")
+    ad = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U3), Rd, ad)
+    alpha = float(host(ad)[0])
+    cfg1 = O.Cfg(dim=1, n=(N,), lo=(0.0,), hi=(2.0,))
+    R1 = O.residual_dirs(cfg1, U1, alpha)
+    assert alpha == O.alpha_max(cfg1, U1) if precision == 0 else abs(alpha / O.alpha_max(cfg1, U1) - 1) < 1e-6
+    Rg = host(Rd)
+    want = np.zeros_like(Rg)
+    want[0] = R1[0, 0, 0][None, None, :]
+    want[1] = R1[1, 0, 0][None, None, :]
+    want[4] = R1[2, 0, 0][None, None, :]
+    if precision == 0:
+        tol = fp64_rhs_tol(cfg3, U3, want, alpha)
+    else:
+        tol = _variation_tol(cfg3, U3, want, alpha)
+    assert (np.abs(Rg - want) <= tol).all()
