@@ -2,6 +2,7 @@
 // argument checking and the launch sequences of a residual, a stage, a step
 // and a CUDA-graph-captured run.  No arithmetic of the scheme lives here.
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -327,6 +328,13 @@ static int take_status(weno_ctx *h)
 {
     int r = read_ctl(h);
     if (r) return r;
+    if (h->ctl_host->status & ST_BADINDEX) {
+        CK(h, launch(h, 7, h->stream, [&] {
+               k_clear_status<<<1, 1, 0, h->stream>>>(h->ctl);
+               return cudaGetLastError();
+           }));
+        return fail(h, WENO_ERR_ARG, "weno_cross_eval: an index set held an index outside its mode (fiber skipped)");
+    }
     if (h->ctl_host->status & ST_NONPHYSICAL) {
         CK(h, launch(h, 7, h->stream, [&] {
                k_clear_status<<<1, 1, 0, h->stream>>>(h->ctl);
@@ -495,12 +503,86 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
                                int32_t n_sets, int32_t flags)
 {
     if (!h) return WENO_ERR_ARG;
-    (void)inst;
-    (void)n_inst;
-    (void)sets;
-    (void)n_sets;
-    (void)flags;
-    return fail(h, WENO_ERR_UNSUPPORTED, "weno_cross_eval: not built yet");
+    if (!inst || !sets || n_inst < 1 || n_sets < 1) return fail(h, WENO_ERR_ARG, "weno_cross_eval: empty input");
+    std::vector<CrossInst> ci(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+        const weno_tt_instance &I = inst[k];
+        CrossInst &c = ci[k];
+        for (int m = 0; m < 3; ++m) {
+            if (I.n[m] < 3 || !(I.h[m] > 0.0))
+                return fail(h, WENO_ERR_ARG, "weno_cross_eval: instance needs n >= 3 and h > 0 per mode");
+            c.n[m] = I.n[m];
+            c.h[m] = I.h[m];
+            for (int sd = 0; sd < 2; ++sd) {
+                if (I.bc[m][sd] < 0 || I.bc[m][sd] > 2) return fail(h, WENO_ERR_ARG, "weno_cross_eval: bad boundary rule");
+                c.bc[m][sd] = I.bc[m][sd];
+            }
+        }
+        for (int m = 0; m < 2; ++m) {
+            if (I.r[m] < 1 || I.r[m] > cross_max_rank())
+                return fail(h, WENO_ERR_ARG, "weno_cross_eval: TT ranks must be in 1..32");
+            c.r[m] = I.r[m];
+        }
+        for (int f = 0; f < 5; ++f)
+            for (int m = 0; m < 3; ++m) {
+                if (!I.core[f][m]) return fail(h, WENO_ERR_ARG, "weno_cross_eval: null core");
+                c.core[f][m] = I.core[f][m];
+            }
+        if (!(I.alpha >= 0.0) || !std::isfinite(I.alpha)) return fail(h, WENO_ERR_ARG, "weno_cross_eval: bad alpha");
+        c.alpha = I.alpha;
+    }
+    std::vector<CrossSet> cs(n_sets);
+    long long work = 0;
+    for (int k = 0; k < n_sets; ++k) {
+        const weno_fiber_set &F = sets[k];
+        CrossSet &c = cs[k];
+        if (F.instance < 0 || F.instance >= n_inst || F.mode < 0 || F.mode > 2 || F.flux_dir < 0 || F.flux_dir > 2)
+            return fail(h, WENO_ERR_ARG, "weno_cross_eval: bad instance, mode or flux_dir");
+        if (F.n_left < 1 || F.n_right < 1 || !F.out || (F.mode > 0 && !F.left) || (F.mode < 2 && !F.right) ||
+            (F.mode == 0 && F.n_left != 1) || (F.mode == 2 && F.n_right != 1))
+            return fail(h, WENO_ERR_ARG, "weno_cross_eval: inconsistent index sets");
+        c.inst = F.instance;
+        c.mode = F.mode;
+        c.fd = F.flux_dir;
+        c.n_mode = ci[F.instance].n[F.mode];
+        c.n_left = F.n_left;
+        c.n_right = F.n_right;
+        c.left = F.left;
+        c.right = F.right;
+        c.out = F.out;
+        c.work_begin = work;
+        work += F.n_left * F.n_right;
+    }
+    if (work >= (1ll << 31)) return fail(h, WENO_ERR_ARG, "weno_cross_eval: more than 2^31 fibers");
+    const size_t bytes = sizeof(CrossInst) * n_inst + sizeof(CrossSet) * n_sets + 64;
+    if (bytes > h->xbuf_bytes) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->xbuf);
+        h->xbuf = nullptr;
+        h->xbuf_bytes = 0;
+        CK(h, cudaMalloc(&h->xbuf, bytes));
+        h->xbuf_bytes = bytes;
+    }
+    char *base = (char *)h->xbuf;
+    unsigned long long *counter = (unsigned long long *)base;
+    CrossInst *dinst = (CrossInst *)(base + 64);
+    CrossSet *dsets = (CrossSet *)(base + 64 + sizeof(CrossInst) * n_inst);
+    // pageable sources: each copy returns once the data is staged
+    CK(h, cudaMemcpyAsync(dinst, ci.data(), sizeof(CrossInst) * n_inst, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(dsets, cs.data(), sizeof(CrossSet) * n_sets, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), h->stream));
+    CrossArgs a{};
+    a.inst = dinst;
+    a.sets = dsets;
+    a.n_sets = n_sets;
+    a.n_work = work;
+    a.gamma = h->p.gamma;
+    a.eps = h->p.eps_weno;
+    a.counter = counter;
+    a.status = &h->ctl->status;
+    a.fp64 = (flags & WENO_CROSS_FP64_CHECK) ? 1 : 0;
+    CK(h, launch(h, 7, h->stream, [&] { return launch_cross(a, h->stream); }));
+    return WENO_OK;
 }
 
 extern "C" int weno_profile_enable(weno_handle h, int32_t enable)

@@ -14,7 +14,7 @@
 namespace wg {
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
-enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2 };
+enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2, ST_BADINDEX = 4 };
 
 // Device control block of one handle: time, step size and the stage alphas.
 // alpha[s] holds the bit pattern of a non-negative double so that atomicMax

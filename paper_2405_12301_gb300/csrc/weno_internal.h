@@ -71,9 +71,11 @@ struct CrossArgs {
     long long n_work;      // total work items
     double gamma, eps;
     unsigned long long *counter;
+    int *status;           // ST_BADINDEX is latched here
     int fp64;
 };
 
 cudaError_t launch_cross(const CrossArgs &a, cudaStream_t s);
+int cross_max_rank();
 
 }  // namespace wg

@@ -305,19 +305,33 @@ def test_bulk_l1_within_1p1_of_fp64_above_floor(W, N):
     assert e32 <= 1.1 * e64
 
 
-def test_bulk_periodic_conservation_drift_is_small(W):
-    cfg = O.Cfg(dim=2, n=(128, 96))
-    U0 = I.random_state(2, (128, 96), seed=17, jumps=True)
+@pytest.mark.parametrize("jumps", [False, True])
+def test_bulk_periodic_conservation_drift_is_bounded(W, jumps):
+    """FP32-bulk conserves up to the FP32 rounding of interface fluxes: an
+    interface on a tile boundary is formed by two CTAs relative to two line
+    references, so each such interface may differ by ~2^-24 V_tile (V_tile the
+    flux variation across a tile).  Per step that moves a sum by at most
+    (cells / S_min) * 2^-24 * V * dt / h, i.e. a relative drift per step of
+    2^-24 * (dt / h) * V / (S_min * mean |U_f|), S_min = 26 cells; the bound
+    below takes V = (1 + alpha) * (range of U_f + range of rho E) and 4x margin."""
+    n = (128, 96)
+    cfg = O.Cfg(dim=2, n=n)
+    U0 = I.random_state(2, n, seed=17, jumps=jumps)
     s = solver(W, cfg, precision=1)
     Ud = dev(U0)
     s0 = np.array(s.sums(Ud))
     s.set_time(0.0)
-    s.run(Ud, 1e9, max_steps=50)
+    steps = 50
+    s.run(Ud, 1e9, max_steps=steps)
     s1 = np.array(s.sums(Ud))
-    scale = np.abs(U0).sum(axis=(1, 2, 3))
-    drift = np.abs(s1 - s0) / scale
-    print("bulk conservation drift after 50 steps:", drift)
-    assert np.all(drift <= 1e-9)
+    alpha = O.alpha_max(cfg, U0)
+    dt_h = 0.5 / alpha
+    for f in range(4):
+        V = (1 + alpha) * (np.ptp(U0[f]) + np.ptp(U0[3]))
+        bound = 4 * steps * 2.0 ** -24 * dt_h * V / (26 * np.abs(U0[f]).mean())
+        drift = abs(s1[f] - s0[f]) / np.abs(U0[f]).sum()
+        print("bulk drift f=%d: %.3e (bound %.3e)" % (f, drift, bound))
+        assert drift <= bound
 
 
 # ----------------------------------------------------- full-size workloads
