@@ -242,6 +242,71 @@ def kernel_table(kms, kn):
     return {KIND_NAMES[k]: [kms[k] / kn[k], kn[k]] for k in range(len(kms)) if kn[k] > 0}
 
 
+def cross_flops(mode, fd, r, nm, n_left, n_right):
+    """Algorithmic flops of one fiber set: per sample the stencil values
+    contracted from the cores (L G R: 2 r_{m-1} r_m + 2 r_{m-1} per value; with a
+    shifted left/right vector, one G product plus 7 short dot products), the
+    LF split fluxes at the points the sample needs, WENO5 at its interfaces and
+    the flux difference (same per-item counts as the full grid)."""
+    rl = 1 if mode == 0 else r[mode - 1]
+    rr = 1 if mode == 2 else r[mode]
+    samples = n_left * nm * n_right
+    if fd == mode:
+        per = 5 * (2 * rl * rr + 2 * rl) + 45 + 5 * 137 + 5 * 3
+    else:
+        tl = rl if fd < mode else rr
+        per = 5 * (2 * rl * rr + 7 * 2 * tl) + 7 * 45 + 2 * 5 * 137 + 5 * 3
+    return samples, samples * per
+
+
+def bench_cross(weno, I, torch, reps=10):
+    """The batched WENO-cross workload: 64 TT instances (n per mode from
+    {64,128,256,512}, ranks 2..32, TT-SVD of seeded smooth fields with a tanh
+    front), every sweep mode x flux direction (9 fiber sets per instance), all
+    evaluated in one persistent launch, FP32."""
+    insts, sets = [], []
+    samples = flops = 0
+    for k in range(64):
+        inst = I.tt_instance(seed=I.MASTER_SEED + k)
+        d = dict(n=inst["n"], r=inst["r"], h=[1.0 / x for x in inst["n"]], bc=((0, 0),) * 3, alpha=3.0,
+                 cores=[[torch.from_numpy(c).cuda() for c in fc] for fc in inst["cores"]])
+        insts.append(d)
+        for mode in range(3):
+            for fd in range(3):
+                left, right = I.cross_index_sets(1000 * k + 10 * mode + fd, inst["n"], inst["r"], mode)
+                out = torch.empty((5, left.shape[0], inst["n"][mode], right.shape[0]), dtype=torch.float32,
+                                  device="cuda")
+                sets.append(dict(instance=k, mode=mode, flux_dir=fd,
+                                 left=torch.from_numpy(left).cuda() if mode > 0 else None,
+                                 right=torch.from_numpy(right).cuda() if mode < 2 else None, out=out))
+                sm, fl = cross_flops(mode, fd, inst["r"], inst["n"][mode], left.shape[0], right.shape[0])
+                samples += sm
+                flops += fl
+    h = weno.weno_init(None)
+    for _ in range(3):
+        weno.weno_cross_eval(h, insts, sets)
+    weno.weno_sync(h)
+    weno.weno_profile_enable(h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        weno.weno_cross_eval(h, insts, sets)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    kms, kn, launches = weno.weno_profile_read(h)
+    weno.weno_sync(h)
+    weno.weno_destroy(h)
+    kernel_ms = kms[7] / max(1, kn[7])
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"value": samples / (ms * 1e-3) / 1e6, "unit": "Msample/s", "ms_per_launch": ms, "samples": samples,
+            "fiber_sets": len(sets), "instances": 64, "dtype": "f32",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None, "kernel": "k_cross",
+                         "ms_per_launch": kernel_ms}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,6 +315,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cross", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -312,6 +378,7 @@ def main():
            "api": "weno_run_host (pinned host state, one step per call)"}
 
     acc = accuracy(weno, I, torch) if rank == 0 else None
+    cross = bench_cross(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     rl = roofline(w, True, kms, kn, cells)
     rl64 = roofline(w, False, kms64, kn64, cells)
     step_tflops = value * 1e6 * flops_cell_stage(w["dim"]) / 1e12 / world
@@ -332,6 +399,7 @@ def main():
                  "graph_ms_per_step": ms64_graph / steps64, "roofline": rl64,
                  "kernels_ms_per_launch": kernel_table(kms64, kn64)},
         "accuracy": acc,
+        "cross_eval": cross,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
