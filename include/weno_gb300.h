@@ -161,9 +161,33 @@ enum { WENO_PROFILE_KINDS = 8 };
 int weno_profile_enable(weno_handle h, int32_t enable);
 int weno_profile_read(weno_handle h, double *ms, int64_t *launches, int64_t *total_launches);
 
+/* Conservation sums for callers that cannot allocate device memory -- for
+ * example a host application or framework that owns all device memory through
+ * its own pool and forbids other allocations, a latency-critical loop in which
+ * cudaMalloc / cudaFree would synchronise the device, or a process that has
+ * already committed its device memory and cannot risk an allocation failing
+ * mid-run.  The paper has no counterpart; it is a deployment convenience.
+ *
+ * Same result as weno_sums (the same fixed-order two-level reduction, so the
+ * same bits), without a handle and without allocating: the per-block partial
+ * sums live in a 40 KiB device array inside the library (1024 blocks x 5
+ * fields), which every device that loads the library keeps until the process
+ * exits.
+ *   U         device FP64 [nf][ncells], caller-owned
+ *   nf        1..5 fields; ncells 1..2^40 cells (anything else: WENO_ERR_ARG)
+ *   sums_dev  device FP64 [nf], caller-owned, written asynchronously
+ *   stream    cudaStream_t to enqueue on (NULL: legacy default stream)
+ * The first call on each device looks up the device address of the scratch
+ * array (with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (different streams, no
+ * ordering between them) race and must not be issued.  Errors are returned as
+ * a status; weno_last_error(NULL) then gives the reason. */
+int weno_sums_noalloc(const double *U, int32_t nf, int64_t ncells, double *sums_dev, void *cuda_stream);
+
 /* Text of the last error on this handle (never NULL; static storage of the
  * handle, valid until the next call on it).  h may be NULL: then it describes
- * the last weno_init failure of this thread. */
+ * the last failure of this thread in weno_init or weno_sums_noalloc. */
 const char *weno_last_error(weno_handle h);
 
 /* ------------------------------------------------------------------------

@@ -83,6 +83,11 @@ template <class F> static cudaError_t launch(weno_ctx *h, int kind, cudaStream_t
 
 static thread_local std::string g_init_error;
 
+namespace wg {
+// Error text for calls made without a handle (read back by weno_last_error(NULL)).
+void set_thread_error(const std::string &msg) { g_init_error = msg; }
+}  // namespace wg
+
 static int fail(weno_ctx *h, int code, const std::string &msg)
 {
     if (h) h->err = msg;

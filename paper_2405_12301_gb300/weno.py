@@ -20,7 +20,8 @@ CROSS_FP64_CHECK = 1
 
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
            "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
-           "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read")
+           "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read",
+           "weno_sums_noalloc")
 PROFILE_KINDS = 8
 
 
@@ -80,6 +81,7 @@ def lib():
         L.weno_cross_eval.argtypes = [vp, P(weno_tt_instance), i32, P(weno_fiber_set), i32, i32]
         L.weno_profile_enable.argtypes = [vp, i32]
         L.weno_profile_read.argtypes = [vp, P(d), P(i64), P(i64)]
+        L.weno_sums_noalloc.argtypes = [vp, i32, i64, vp, vp]
         for name in EXPORTS:
             if name != "weno_last_error":
                 getattr(L, name).restype = C.c_int
@@ -188,6 +190,18 @@ def weno_sums(h, U, nf):
     out = (C.c_double * nf)()
     _check(h, lib().weno_sums(h, _ptr(U, torch.float64), out))
     return list(out)
+
+
+def weno_sums_noalloc(U, sums_out, stream=None):
+    """Conservation sums into the device tensor sums_out (nf doubles) without any
+    device allocation; U is [nf, ...] FP64 on the current device."""
+    import torch
+    nf = U.shape[0]
+    code = lib().weno_sums_noalloc(_ptr(U, torch.float64), nf, U.numel() // nf, _ptr(sums_out, torch.float64),
+                                   stream if stream is not None else _stream())
+    if code != OK:
+        raise WenoError(code, lib().weno_last_error(None).decode())
+    return code
 
 
 def weno_sync(h):
