@@ -218,13 +218,25 @@ def time_precision(weno, I, torch, w, prec, steps, warmup, dist, world):
     return ms, kms, kn, launches, ms_graph
 
 
+def kind_flops(D, k):
+    """Algorithmic flops per cell of one launch of profile kind k."""
+    if k == 2:   # fused x+y of a 3D plane: two directions, no epilogue
+        return 2 * flops_sweep(D, False)
+    if k == 3:   # 1D sweep ending the stage
+        return flops_sweep(1, True)
+    if k == 4:   # fused x+y of a 2D grid ending the stage
+        return flops_sweep(2, False) + flops_sweep(2, True)
+    if k == 5:   # z sweep ending a 3D stage
+        return flops_sweep(3, True)
+    return flops_sweep(D, False)
+
+
 def roofline(w, prec_bulk, kms, kn, cells):
     D = w["dim"]
     kinds = [k for k in range(6) if kn[k] > 0]
     k = max(kinds, key=lambda i: kms[i])
-    last = k >= 3
     per_launch_ms = kms[k] / kn[k]
-    flops = cells * flops_sweep(D, last)
+    flops = cells * kind_flops(D, k)
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     peak = PEAK_FP32_TFLOPS if prec_bulk else PEAK_FP64_TFLOPS
     names = KIND_NAMES
@@ -235,7 +247,7 @@ def roofline(w, prec_bulk, kms, kn, cells):
             else "nominal GB300 FP64 1.25 TFLOP/s"}
 
 
-KIND_NAMES = ["sweep_x", "sweep_y", "sweep_z", "sweep_x_last", "sweep_y_last", "sweep_z_last", "alpha", "small"]
+KIND_NAMES = ["unused0", "unused1", "xy_plane_3d", "sweep_x_1d", "xy_fused_2d", "sweep_z_3d", "alpha", "small"]
 
 
 def kernel_table(kms, kn):

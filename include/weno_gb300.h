@@ -151,9 +151,11 @@ int weno_sync(weno_handle h);
  * (weno_rhs, weno_ssprk3_step, weno_run with graph_steps <= 0) record a CUDA
  * event pair around every kernel on the handle's stream; weno_profile_read
  * (synchronises) adds the elapsed times up per kernel kind:
- *   kind 0..2: sweep of direction d that stores/adds to the accumulator,
- *   kind 3..5: last sweep of a stage (direction d, stage combination or L(U)),
- *   kind 6: wavespeed max, kind 7: step control and other small kernels.
+ *   kind 2: fused x+y kernel of a 3D grid (stores to the accumulator),
+ *   kind 3: 1D sweep, kind 4: fused x+y kernel of a 2D grid, kind 5: z sweep
+ *           of a 3D grid (3..5 end a residual: stage combination or L(U)),
+ *   kind 6: wavespeed max, kind 7: step control and other small kernels
+ *   (kinds 0 and 1 are unused).
  * ms and launches (host arrays of WENO_PROFILE_KINDS) receive the totals since
  * the last enable; *total_launches counts every kernel this handle launched
  * (graphs included) since the last enable. */

@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     T *sF = reinterpret_cast<T *>(smem + L::F_off);
     RefState<D> *sref = reinterpret_cast<RefState<D> *>(smem + L::ref_off);
 
-    const double dt = a.ctl->dt;
-    if (a.check_dt && dt == 0.0) return;  // the step is a no-op (time reached t_end)
+    const long long dtbits = __double_as_longlong(a.ctl->dt);
+    if (a.check_dt && dtbits == 0) return;  // the step is a no-op (time reached t_end)
+    const double dt = __longlong_as_double(dtbits);
 
     const long long N = a.N;
     const int n = a.n[DIR];
@@ -79,8 +80,9 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     };
 
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    const float alpha_f = BULK ? f64_to_f32(alpha) : 0.0f;  // integer pipe: cvt issues at FP64 rate
     const double gm1 = a.gamma - 1.0;
-    const T eps = (T)a.eps;
+    const T eps = BULK ? (T)a.eps_f : (T)a.eps;
 
     // ---- phase 0 (FP32-bulk): reference state of every line
     if (BULK) {
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
 #pragma unroll
             for (int f = 0; f < NF; ++f)
                 q[f] = ok ? a.U[f * N + base + (long long)cr * st] : (f == 0 || f == NF - 1 ? 1.0 : 0.0);
-            make_ref<D>(q, (float)gm1, sref[w]);
+            make_ref<D>(q, a.gm1_f, sref[w]);
         }
         __syncthreads();
     }
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
             if constexpr (BULK) {
                 float dq[NF];
                 diff_from_ref<D>(q, sref[w], dq);
-                split_flux_diff<D, DIR>(dq, sref[w], (float)alpha, (float)gm1, fpv, fmv);
+                split_flux_diff<D, DIR>(dq, sref[w], alpha_f, a.gm1_f, fpv, fmv);
             } else {
                 split_flux_f64<D, DIR>(q, alpha, gm1, fpv, fmv);
             }
@@ -155,15 +157,15 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     __syncthreads();
 
     // ---- phase C: flux difference and epilogue
-    const T ih = (T)a.inv_h[DIR];
+    const T ih = BULK ? (T)a.inv_h_f[DIR] : (T)a.inv_h[DIR];
     double cmax = 0.0;
     float cmaxf = 0.0f;
     bool bad = false;
     // stage combination coefficients (Eq. tt-ssprk3): U' = a_n U^n + b_n (U^k + dt R)
     const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
     const double bn = a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0);
-    const float anf = (float)an;
-    const float bdtf = (float)(bn * dt);
+    const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
+    const float bdtf = BULK ? f64_to_f32(bn * dt) : 0.0f;
     for (int u = threadIdx.x; u < W * S; u += NT) {
         int w, i;
         if (DIR == 0) { w = u / S; i = u - w * S; }
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
                     float qf[NF];
 #pragma unroll
                     for (int f = 0; f < NF; ++f) qf[f] = f64_to_f32(out[f]);
-                    cmaxf = fmaxf(cmaxf, wavespeed_f32<D>(qf, (float)a.gamma, b));
+                    cmaxf = fmaxf(cmaxf, wavespeed_f32<D>(qf, a.gamma_f, b));
                 } else {
                     cmax = fmax(cmax, wavespeed_f64<D>(out, a.gamma, b));
                 }
@@ -255,9 +257,8 @@ static cudaError_t attr_t()
                                 (int)L::bytes);
 }
 
-#define WG_SWEEP_TABLE(X, B)                                                                              \
-    X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE) X(2, 0, B, EPI_STORE) X(2, 1, B, EPI_RHS) X(2, 1, B, EPI_STAGE) \
-        X(3, 0, B, EPI_STORE) X(3, 1, B, EPI_ADD) X(3, 2, B, EPI_RHS) X(3, 2, B, EPI_STAGE)
+// 1D grids, and the z direction of 3D grids (x and y run in the fused k_xy kernel).
+#define WG_SWEEP_TABLE(X, B) X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE) X(3, 2, B, EPI_RHS) X(3, 2, B, EPI_STAGE)
 
 cudaError_t sweep_set_attributes()
 {

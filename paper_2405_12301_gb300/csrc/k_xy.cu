@@ -1,0 +1,327 @@
+// k_xy.cu -- fused x+y residual kernel of the WENO5-JS scheme for 2D grids
+// and for each z-plane of 3D grids.
+//
+// A CTA (256 threads) owns a TX x TY = 32 x 8 tile of one plane, one cell per
+// thread, and the plus-shaped halo around it (three ghost layers per side in x
+// and in y, Sec. 4.5).  Phases, all through shared memory:
+//   A+F. every point of the tile and halo is loaded once (boundary rule applied
+//      to ghost indices; FP32-bulk takes its difference from the tile's
+//      reference state) and its LF split fluxes f(+/-) (Sec. 2.2) are formed in
+//      the directions that need them: each thread its own point in x and y, and
+//      one halo point in the halo's direction;
+//   W. every x- and y-interface flux of the tile is reconstructed once: each
+//      thread its cell's left and bottom faces for every component, and the
+//      tile's last column/row faces spread over the threads; WENO(+) plus
+//      mirrored WENO(-);
+//   C. each thread forms -(dF/dx) - (dG/dy) for its cell (Sec. 4.1) and either
+//      stores it (3D: the z sweep adds its part and runs the stage), writes L(U),
+//      or applies the SSP-RK3 stage combination (Eq. tt-ssprk3 without rounding)
+//      and publishes the wavespeed max of the new state.
+// Compared with one launch per direction, each point is loaded and split once
+// per stage, and in 2D the residual never leaves the SM.
+#include <type_traits>
+
+#include "weno_dev.cuh"
+#include "weno_internal.h"
+
+namespace wg {
+
+namespace xy {
+constexpr int NT = 256;
+constexpr int TX = 32, TY = 8;
+constexpr int BX = TX + 6, BY = TY + 6;     // row and column extents with halo
+constexpr int NXP = BX * TY;                // x-flux points: 38 x 8
+constexpr int NYP = TX * BY;                // y-flux points: 32 x 14
+constexpr int NXI = (TX + 1) * TY;          // x interfaces: 33 x 8
+constexpr int NYI = TX * (TY + 1);          // y interfaces: 32 x 9
+constexpr int NHY = 6 * TX;                 // y-halo points (rows -3..-1, TY..TY+2)
+constexpr int NHALO = NHY + 6 * TY;         // plus x-halo points: 240
+
+template <int D, bool BULK> struct Layout {
+    using T = typename std::conditional<BULK, float, double>::type;
+    static constexpr int NF = D + 2;
+    static constexpr size_t F_off = 0;                                        // Fx, Fy
+    static constexpr size_t fx_off = (sizeof(T) * NF * (NXI + NYI) + 15) & ~size_t(15);
+    static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXP;
+    static constexpr size_t ref_off = (fy_off + sizeof(T) * 2 * NF * NYP + 15) & ~size_t(15);
+    static constexpr size_t bytes = ref_off + sizeof(RefState<D>);
+};
+}  // namespace xy
+
+template <int D, bool BULK, int EPI>
+__global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
+{
+    using namespace xy;
+    using L = Layout<D, BULK>;
+    using T = typename L::T;
+    constexpr int NF = L::NF;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *Fx = reinterpret_cast<T *>(smem + L::F_off);        // [NF][TY][TX+1]
+    T *Fy = Fx + NF * NXI;                                 // [NF][TY+1][TX]
+    T *fx = reinterpret_cast<T *>(smem + L::fx_off);       // [2][NF][TY][BX]
+    T *fy = reinterpret_cast<T *>(smem + L::fy_off);       // [2][NF][BY][TX]
+    RefState<D> &ref = *reinterpret_cast<RefState<D> *>(smem + L::ref_off);
+
+    // dt and alpha come from the control block; the FP32 path converts them on
+    // the integer pipe (a cvt issues at FP64 rate on this GPU)
+    const long long dtbits = __double_as_longlong(a.ctl->dt);
+    if (a.check_dt && dtbits == 0) return;
+    const double dt = __longlong_as_double(dtbits);
+    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+
+    const int nx = a.n[0], ny = a.n[1];
+    const long long N = a.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long long zoff = (long long)blockIdx.z * a.stride[2];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < nx && gy < ny;
+    const long long cell = zoff + (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
+
+    // the stage combination needs U^n at this thread's cell: issue the loads now
+    double un[NF];
+    if (EPI == EPI_STAGE && a.stage > 0) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
+    }
+
+    // ---- reference state of the tile (FP32-bulk): its first cell
+    if (BULK) {
+        if (threadIdx.x < 32) {
+            const long long c0 = zoff + (long long)(y0 < ny ? y0 : ny - 1) * nx + (x0 < nx ? x0 : nx - 1);
+            double q[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
+            RefState<D> r;
+            make_ref<D>(q, a.gm1_f, r);
+            if (threadIdx.x == 0) ref = r;
+        }
+        __syncthreads();
+    }
+    const T al = BULK ? (T)f64_to_f32(alpha) : (T)alpha;
+    const double gm1 = a.gamma - 1.0;
+    // interior tiles (halo inside the grid) skip the boundary rule
+    const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
+
+    auto load_point = [&](int lx, int ly, double *q) {
+        int cx = x0 + lx, cy = y0 + ly;
+        bool fx_ = false, fy_ = false;
+        if (!interior) {
+            cx = cx < nx + 2 ? cx : nx + 2;
+            cy = cy < ny + 2 ? cy : ny + 2;
+            cx = ghost_source(cx, nx, a.bc[0][0], a.bc[0][1], fx_);
+            cy = ghost_source(cy, ny, a.bc[1][0], a.bc[1][1], fy_);
+        }
+        const double *src = a.U + zoff + (long long)cy * nx + cx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) q[f] = __ldg(src + f * N);
+        if (fx_) q[1] = -q[1];
+        if (fy_) q[2] = -q[2];
+    };
+    // split flux of a point in direction DIR, stored at its slot of fx / fy
+    auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
+        T fp[NF], fm[NF];
+        if constexpr (BULK) {
+            if (dirx) split_flux_diff<D, 0>(q, ref, al, a.gm1_f, fp, fm);
+            else split_flux_diff<D, 1>(q, ref, al, a.gm1_f, fp, fm);
+        } else {
+            if (dirx) split_flux_f64<D, 0>(q, al, gm1, fp, fm);
+            else split_flux_f64<D, 1>(q, al, gm1, fp, fm);
+        }
+        if (dirx) {
+            const int o = ly * BX + (lx + 3);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                fx[f * NXP + o] = fp[f];
+                fx[(NF + f) * NXP + o] = fm[f];
+            }
+        } else {
+            const int o = (ly + 3) * TX + lx;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                fy[f * NYP + o] = fp[f];
+                fy[(NF + f) * NYP + o] = fm[f];
+            }
+        }
+    };
+
+    // ---- phase A+F: own point (x and y fluxes) and one halo point per thread
+    double uk[NF];                // U^(k) at the own cell, kept for the stage combination
+    float hk[NF], lk[NF];         // its hi/lo split (FP32-bulk)
+    load_point(tx, ty, uk);
+    {
+        T q[NF];
+        if constexpr (BULK) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                split_f64(uk[f], hk[f], lk[f]);
+                q[f] = (hk[f] - ref.hi[f]) + (lk[f] - ref.lo[f]);
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = uk[f];
+        }
+        flux_store(q, true, tx, ty);
+        flux_store(q, false, tx, ty);
+    }
+    if (threadIdx.x < NHALO) {
+        int t = threadIdx.x, lx, ly;
+        bool dirx;
+        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
+            lx = t & 31;
+            const int k = t >> 5;
+            ly = k < 3 ? k - 3 : TY + k - 3;
+            dirx = false;
+        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
+            t -= NHY;
+            ly = t / 6;
+            const int k = t - ly * 6;
+            lx = k < 3 ? k - 3 : TX + k - 3;
+            dirx = true;
+        }
+        double qd[NF];
+        load_point(lx, ly, qd);
+        T q[NF];
+        if constexpr (BULK) diff_from_ref<D>(qd, ref, q);
+        else {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = qd[f];
+        }
+        flux_store(q, dirx, lx, ly);
+    }
+    __syncthreads();
+
+    // ---- phase W: own left x face and bottom y face for every component, plus
+    // one of the remaining faces (top of the tile's top row, right of its last column)
+    const T eps = BULK ? (T)a.eps_f : (T)a.eps;
+    auto face_x = [&](int f, int ly, int j) -> T {  // between local columns j-1 and j of row ly
+        const T *P = fx + f * NXP + ly * BX;
+        const T *M = fx + (NF + f) * NXP + ly * BX;
+        return weno5<T>(P[j], P[j + 1], P[j + 2], P[j + 3], P[j + 4], eps) +
+               weno5<T>(M[j + 5], M[j + 4], M[j + 3], M[j + 2], M[j + 1], eps);
+    };
+    auto face_y = [&](int f, int lx, int j) -> T {  // between local rows j-1 and j of column lx
+        const T *P = fy + f * NYP + lx;
+        const T *M = fy + (NF + f) * NYP + lx;
+        return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
+               weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
+    };
+    T fxl[NF], fyb[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        fxl[f] = face_x(f, ty, tx);
+        Fx[f * NXI + ty * (TX + 1) + tx] = fxl[f];
+        fyb[f] = face_y(f, tx, ty);
+        Fy[f * NYI + ty * TX + tx] = fyb[f];
+    }
+    if (threadIdx.x < NF * (TX + TY)) {
+        const int t = threadIdx.x;
+        if (t < NF * TX) {
+            const int f = t >> 5, lx = t & 31;
+            Fy[f * NYI + TY * TX + lx] = face_y(f, lx, TY);
+        } else {
+            const int u = t - NF * TX;
+            const int f = u >> 3, ly = u & 7;
+            Fx[f * NXI + ly * (TX + 1) + TX] = face_x(f, ly, TX);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase C: the cell's residual -(dF/dx) - (dG/dy) and the epilogue
+    const T ihx = BULK ? (T)a.inv_h_f[0] : (T)a.inv_h[0];
+    const T ihy = BULK ? (T)a.inv_h_f[1] : (T)a.inv_h[1];
+    T r[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const T dx = Fx[f * NXI + ty * (TX + 1) + tx + 1] - fxl[f];
+        const T dy = Fy[f * NYI + (ty + 1) * TX + tx] - fyb[f];
+        r[f] = -dx * ihx - dy * ihy;
+    }
+    if (EPI == EPI_STORE) {
+        if (own) {
+            T *acc = reinterpret_cast<T *>(a.acc);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f * N + cell] = r[f];
+        }
+        return;
+    }
+    if (EPI == EPI_RHS) {
+        if (own) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                if constexpr (BULK) a.Rout[f * N + cell] = f32_to_f64(r[f]);
+                else a.Rout[f * N + cell] = r[f];
+            }
+        }
+        return;
+    }
+    // EPI_STAGE: U' = a_n U^n + b_n (U^k + dt R)
+    if constexpr (BULK) {
+        // U' = U^k + D, D = a_n (U^n - U^k) + b_n dt R in FP32 from hi/lo differences
+        float s = 0.0f;
+        bool bad = false;
+        if (own) {
+            const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
+            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            float qn[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                float dl = bdt * r[f];
+                if (a.stage > 0) {
+                    float hn, ln;
+                    split_f64(un[f], hn, ln);
+                    dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
+                }
+                a.Uout[f * N + cell] = uk[f] + f32_to_f64(dl);
+                qn[f] = hk[f] + (lk[f] + dl);
+            }
+            s = wavespeed_f32<D>(qn, a.gamma_f, bad);
+        }
+        block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+    } else {
+        double cmax = 0.0;
+        bool bad = false;
+        if (own) {
+            const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
+            const double bn = a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0);
+            double out[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const double sf = uk[f] + dt * r[f];
+                out[f] = a.stage == 0 ? sf : an * un[f] + bn * sf;
+                a.Uout[f * N + cell] = out[f];
+            }
+            cmax = wavespeed_f64<D>(out, a.gamma, bad);
+        }
+        block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+    }
+}
+
+template <int D, bool BULK, int EPI>
+static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
+{
+    using L = xy::Layout<D, BULK>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_xy<D, BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L::bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)((a.n[0] + xy::TX - 1) / xy::TX), (unsigned)((a.n[1] + xy::TY - 1) / xy::TY),
+              (unsigned)a.n[2]);
+    k_xy<D, BULK, EPI><<<grid, xy::NT, L::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
+{
+#define X(D, B, E) \
+    if (dim == D && bulk == B && epi == E) return launch_xy_t<D, B, E>(a, s);
+    X(2, false, EPI_RHS) X(2, false, EPI_STAGE) X(3, false, EPI_STORE)
+    X(2, true, EPI_RHS) X(2, true, EPI_STAGE) X(3, true, EPI_STORE)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace wg

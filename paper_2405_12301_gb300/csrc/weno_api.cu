@@ -275,19 +275,28 @@ static SweepArgs base_args(weno_ctx *h)
     a.stride[2] = h->n[0] * h->n[1];
     a.gamma = h->p.gamma;
     a.eps = h->p.eps_weno;
+    a.gamma_f = (float)h->p.gamma;
+    a.gm1_f = (float)(h->p.gamma - 1.0);
+    a.eps_f = (float)h->p.eps_weno;
+    for (int d = 0; d < 3; ++d) a.inv_h_f[d] = (float)a.inv_h[d];
     a.acc = h->acc;
     return a;
 }
 
 static bool bulk(const weno_ctx *h) { return h->p.precision == WENO_FP32_BULK; }
 
-// All directions of one residual evaluation; the last one runs epilogue `last`.
+// One residual evaluation; the last kernel runs epilogue `last`.
+//   1D: the x sweep.  2D: the fused x+y tile kernel.  3D: the fused x+y kernel
+//   per z-plane (stores), then the z sweep (adds, and runs `last`).
 static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
 {
-    for (int d = 0; d < h->dim; ++d) {
-        const int epi = d == h->dim - 1 ? last : (d == 0 ? EPI_STORE : EPI_ADD);
-        CK(h, launch(h, (epi == EPI_STAGE || epi == EPI_RHS) ? 3 + d : d, s,
-                     [&] { return launch_sweep(h->dim, d, bulk(h), epi, a, s); }));
+    if (h->dim == 1) {
+        CK(h, launch(h, 3, s, [&] { return launch_sweep(1, 0, bulk(h), last, a, s); }));
+    } else if (h->dim == 2) {
+        CK(h, launch(h, 4, s, [&] { return launch_xy(2, bulk(h), last, a, s); }));
+    } else {
+        CK(h, launch(h, 2, s, [&] { return launch_xy(3, bulk(h), EPI_STORE, a, s); }));
+        CK(h, launch(h, 5, s, [&] { return launch_sweep(3, 2, bulk(h), last, a, s); }));
     }
     return WENO_OK;
 }
@@ -460,7 +469,9 @@ extern "C" int weno_run(weno_handle h, double *U, double t_end, double dt, int64
             CK(h, cudaGraphLaunch(h->gexec, h->stream));
             h->launches += h->g_kernels;
         } else {
-            for (int k = 0; k < chunk; ++k)
+            // plain launches: enqueue no step beyond max_steps
+            const long long left = max_steps - (h->ctl_host->steps - s0);
+            for (long long k = 0; k < chunk && k < left; ++k)
                 if ((r = enqueue_step(h, U, h->stream))) return r;
         }
         if ((r = read_ctl(h))) return r;

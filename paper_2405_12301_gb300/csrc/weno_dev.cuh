@@ -38,25 +38,25 @@ struct Ctl {
 // ----------------------------------------------------------------- conversions
 
 // Splits a finite FP64 x into FP32 hi + lo: hi is x truncated to 24 significant
-// bits, lo approximates x - hi (the next 23 bits).  Integer pipe plus one FSUB.
-// |x| below 2^-103 gives lo = 0; below 2^-126, hi = +-0; above FP32 range,
-// hi = +-inf (the callers flag such states as non-physical).
+// bits, lo approximates x - hi (the next 23 bits), on the integer pipe plus one
+// FSUB.  hi: a funnel shift lines the exponent and mantissa up with the FP32
+// fields and one add rebiases the exponent by 1023 - 127.  lo: the low 29
+// mantissa bits m29 are worth m29 * 2^(e-1075); 2^E (1 + (m29 >> 6) / 2^23) with
+// E = e - 1046, minus 2^E, gives that value (exact, up to the 6 dropped bits).
+// |x| < 2^-103 (and zero) gives hi = lo = +-0; |x| >= 2^128 is not representable
+// (states that large are non-physical).
 __device__ __forceinline__ void split_f64(double x, float &hi, float &lo)
 {
     const unsigned xh = (unsigned)__double2hiint(x);
     const unsigned xl = (unsigned)__double2loint(x);
-    const unsigned e = (xh >> 20) & 0x7FFu;
     const unsigned sgn = xh & 0x80000000u;
-    const unsigned hb = sgn | ((e - 896u) << 23) | ((xh & 0xFFFFFu) << 3) | (xl >> 29);
-    // lo = m29 * 2^(e-1075), m29 the low 29 mantissa bits: build 2^E (1 + (m29>>6)/2^23)
-    // with E = e - 1046 and subtract 2^E (exact).
-    const unsigned eb = (e - 919u) << 23;
-    const float fa = __uint_as_float(eb | ((xl & 0x1FFFFFFFu) >> 6));
-    const float fe = __uint_as_float(eb);
-    const float l = fa - fe;
-    const bool hi_ok = (e >= 897u) & (e <= 1150u);
-    hi = hi_ok ? __uint_as_float(hb) : __uint_as_float(e < 897u ? sgn : (sgn | 0x7F800000u));
-    lo = (hi_ok & (e >= 920u)) ? __uint_as_float(__float_as_uint(l) | sgn) : 0.0f;
+    const unsigned fs = __funnelshift_l(xl, xh, 3) + 0x40000000u;  // [e - 896 : 8][mantissa : 23]
+    const unsigned hb = (fs & 0x7FFFFFFFu) | sgn;
+    const unsigned eb = (fs - 0x0B800000u) & 0x7F800000u;          // exponent field of 2^(e - 1046)
+    const float l = __uint_as_float(eb | ((xl >> 6) & 0x7FFFFFu)) - __uint_as_float(eb);
+    const bool ok = ((xh >> 20) & 0x7FFu) >= 920u;
+    hi = __uint_as_float(ok ? hb : sgn);
+    lo = __uint_as_float(ok ? (__float_as_uint(l) | sgn) : sgn);
 }
 
 // FP32 -> FP64, exact for normal numbers (subnormals flush to +-0).
@@ -118,28 +118,33 @@ template <> __device__ __forceinline__ float div_<float>(float a, float b) { ret
 
 // Value at x_{i+1/2} reconstructed from (a, b, c, d, e) = v_{i-2}, ..., v_{i+2}
 // (Sec. 2.2): candidates v^(r), smoothness indicators beta_r, weights
-// alpha_r = d_r / (beta_r + eps)^2 normalised to sum one.  The normalisation is
-// folded into one division: with g_r = (beta_r + eps)^2,
-//   sum_r omega_r v^(r) = sum_r d_r g_s g_t (6 v^(r)) / (6 sum_r d_r g_s g_t),
-// {s, t} the other two indices, which is the same quantity.
+// alpha_r = d_r / (beta_r + eps)^2 normalised to sum one.  Written on the
+// first differences D1..D4 (D1 = b - a, ..., D4 = e - d), in which
+//   beta_0 = 13/12 (D4 - D3)^2 + 1/4 (D4 - 3 D3)^2,
+//   beta_1 = 13/12 (D3 - D2)^2 + 1/4 (D2 + D3)^2,
+//   beta_2 = 13/12 (D2 - D1)^2 + 1/4 (3 D2 - D1)^2,
+//   v^(1) = c + (D2 + 2 D3)/6,  v^(0) - v^(1) = (t1 - t0)/6,  v^(2) - v^(1) = -2 (t1 - t2)/6,
+// t_r the second differences above, so with w_r = d_r g_s g_t (g = (beta + eps)^2,
+// {s, t} the other two indices; w_r / sum w = omega_r)
+//   sum_r omega_r v^(r) = c + [(D2 + 2 D3) sum w + w_0 (t1 - t0) - 2 w_2 (t1 - t2)] / (6 sum w),
+// the same quantity with one division.
 template <typename T>
 __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps)
 {
+    const T D1 = b - a, D2 = c - b, D3 = d - c, D4 = e - d;
+    const T t0 = D4 - D3, t1 = D3 - D2, t2 = D2 - D1;
+    const T s0 = fma(T(-3), D3, D4), s1 = D2 + D3, s2 = fma(T(3), D2, -D1);
     const T k13 = T(13.0 / 12.0), q = T(0.25);
-    const T t0 = c - T(2) * d + e, s0 = T(3) * c - T(4) * d + e;
-    const T t1 = b - T(2) * c + d, s1 = b - d;
-    const T t2 = a - T(2) * b + c, s2 = a - T(4) * b + T(3) * c;
-    T g0 = k13 * t0 * t0 + q * s0 * s0 + eps;
-    T g1 = k13 * t1 * t1 + q * s1 * s1 + eps;
-    T g2 = k13 * t2 * t2 + q * s2 * s2 + eps;
+    T g0 = fma(k13 * t0, t0, fma(q * s0, s0, eps));
+    T g1 = fma(k13 * t1, t1, fma(q * s1, s1, eps));
+    T g2 = fma(k13 * t2, t2, fma(q * s2, s2, eps));
     g0 *= g0;
     g1 *= g1;
     g2 *= g2;
     const T w0 = T(0.3) * (g1 * g2), w1 = T(0.6) * (g0 * g2), w2 = T(0.1) * (g0 * g1);
-    const T p0 = T(2) * c + T(5) * d - e;
-    const T p1 = -b + T(5) * c + T(2) * d;
-    const T p2 = T(2) * a - T(7) * b + T(11) * c;
-    return div_<T>(w0 * p0 + w1 * p1 + w2 * p2, T(6) * (w0 + w1 + w2));
+    const T sw = w0 + w1 + w2;
+    const T num = fma(w0, t1 - t0, fma(T(-2) * w2, t1 - t2, fma(T(2), D3, D2) * sw));
+    return c + div_<T>(num, T(6) * sw);
 }
 
 // ----------------------------------------------------------- point fluxes
@@ -277,6 +282,30 @@ __device__ __forceinline__ float wavespeed_f32(const float *q, float gamma, bool
     const float p = (gamma - 1.0f) * (q[D + 1] - 0.5f * rho * u2);
     bad = !(rho > 0.0f) || !(p > 0.0f) || !isfinite(u2) || !isfinite(q[D + 1]);
     return bad ? 0.0f : sqrtf(u2) + sqrtf(gamma * p * ir);
+}
+
+// FP32 variant for the FP32-bulk kernels: the max runs on the bit patterns of
+// the non-negative floats with the single-instruction warp reduction, and only
+// the block's result is widened to FP64 (on the integer pipe).
+__device__ __forceinline__ void block_max_publish_f32(float v, bool bad, unsigned long long *slot, int *status)
+{
+    __shared__ unsigned warp_max[32];
+    __shared__ int any_bad;
+    if (threadIdx.x == 0) any_bad = 0;
+    const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(v));
+    __syncthreads();
+    if (bad) any_bad = 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_max[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        const unsigned mm = __reduce_max_sync(0xFFFFFFFFu, lane < nw ? warp_max[lane] : 0u);
+        if (lane == 0) {
+            if (mm > 0u) atomicMax(slot, (unsigned long long)__double_as_longlong(f32_to_f64(__uint_as_float(mm))));
+            if (any_bad) atomicOr(status, ST_NONPHYSICAL);
+        }
+    }
 }
 
 // Block-wide max of a non-negative value, then one atomicMax per block on the

@@ -24,6 +24,8 @@ struct SweepArgs {
     double inv_h[3];
     double gamma;
     double eps;
+    float gamma_f, gm1_f, eps_f;  // the same constants in FP32, rounded on the host
+    float inv_h_f[3];
     int stage;           // 0, 1, 2
     int slot_in;         // alpha slot used for the splitting
     int slot_out;        // alpha slot the EPI_STAGE epilogue publishes to
@@ -33,6 +35,8 @@ struct SweepArgs {
 // Launches the sweep of direction dir for a dim-dimensional grid.
 cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 cudaError_t sweep_set_attributes();
+// Fused x+y residual of a 2D grid (EPI_RHS / EPI_STAGE) or of the z-planes of a 3D grid (EPI_STORE).
+cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 
 cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
                          cudaStream_t s);

@@ -133,12 +133,12 @@ def tt_svd3(X, r1, r2):
     compared against the full tensor)."""
     import torch
     n2, n1, n0 = X.shape
+    dev = X.device
+    eigh = lambda G: torch.linalg.eigh(G.cpu())[1].to(dev)  # small Gram matrices: eigh on the host
     A = X.permute(2, 1, 0).reshape(n0, n1 * n2)             # [i, (j,k)]
-    _, V = torch.linalg.eigh(A @ A.T)
-    V1 = V[:, -r1:]                                          # [n0, r1]
+    V1 = eigh(A @ A.T)[:, -r1:]                              # [n0, r1]
     B = (V1.T @ A).reshape(r1 * n1, n2)                      # [(a,j), k]
-    _, V3 = torch.linalg.eigh(B.T @ B)
-    V3 = V3[:, -r2:]                                         # [n2, r2]
+    V3 = eigh(B.T @ B)[:, -r2:]                              # [n2, r2]
     C2 = (B @ V3).reshape(r1, n1, r2)                        # [a, j, b]
     return V1.reshape(n0, 1, r1), C2.permute(1, 0, 2).contiguous(), V3.reshape(n2, r2, 1)
 
