@@ -236,12 +236,15 @@ typedef struct {
 
 enum { WENO_CROSS_FP64_CHECK = 1 };
 
-/* Evaluates every fiber set in one persistent launch on the handle's stream.
- * inst, sets: HOST arrays (copied into the handle's scratch; the device arrays
- * they point to must stay valid until the work completes).  Uses the handle's
- * gamma and eps_weno.  flags: WENO_CROSS_FP64_CHECK evaluates in FP64 and
- * writes FP64 outputs.  Errors: WENO_ERR_ARG for inconsistent sizes or ranks
- * above 64. */
+/* Evaluates every fiber set on the handle's stream: one launch contracts the
+ * left and right TT vectors of every set, one persistent launch evaluates all
+ * samples of all sets.  inst, sets: HOST arrays (copied into the handle's
+ * scratch; the device arrays they point to must stay valid until the work
+ * completes).  Uses the handle's gamma and eps_weno.  flags:
+ * WENO_CROSS_FP64_CHECK evaluates in FP64 and writes FP64 outputs.  Errors:
+ * WENO_ERR_ARG for inconsistent sizes or ranks above 32; an index set holding
+ * an index outside its mode is found on the device, its set is skipped, and
+ * the next synchronising call returns WENO_ERR_ARG. */
 int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, const weno_fiber_set *sets,
                     int32_t n_sets, int32_t flags);
 

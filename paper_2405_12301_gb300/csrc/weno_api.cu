@@ -548,7 +548,7 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
         c.alpha = I.alpha;
     }
     std::vector<CrossSet> cs(n_sets);
-    long long work = 0;
+    long long work = 0, nvec = 0;
     for (int k = 0; k < n_sets; ++k) {
         const weno_fiber_set &F = sets[k];
         CrossSet &c = cs[k];
@@ -567,10 +567,21 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
         c.right = F.right;
         c.out = F.out;
         c.work_begin = work;
-        work += F.n_left * F.n_right;
+        // a work item fixes the index of the side the stencil does not move
+        work += F.flux_dir > F.mode ? F.n_left : F.n_right;
+        c.nsl = F.flux_dir < F.mode ? 7 : 1;
+        c.nsr = F.flux_dir > F.mode ? 7 : 1;
+        c.lvec_off = nvec;
+        nvec += F.n_left * c.nsl * 5 * cross_vec_len();
+        c.rvec_off = nvec;
+        nvec += F.n_right * c.nsr * 5 * cross_vec_len();
     }
-    if (work >= (1ll << 31)) return fail(h, WENO_ERR_ARG, "weno_cross_eval: more than 2^31 fibers");
-    const size_t bytes = sizeof(CrossInst) * n_inst + sizeof(CrossSet) * n_sets + 64;
+    if (work >= (1ll << 31)) return fail(h, WENO_ERR_ARG, "weno_cross_eval: more than 2^31 work items");
+    const size_t esz = (flags & WENO_CROSS_FP64_CHECK) ? sizeof(double) : sizeof(float);
+    const size_t off_inst = 64 + ((sizeof(int) * n_sets + 15) & ~size_t(15));
+    const size_t off_sets = off_inst + ((sizeof(CrossInst) * n_inst + 15) & ~size_t(15));
+    const size_t off_vecs = off_sets + ((sizeof(CrossSet) * n_sets + 15) & ~size_t(15));
+    const size_t bytes = off_vecs + esz * (size_t)nvec;
     if (bytes > h->xbuf_bytes) {
         CK(h, cudaStreamSynchronize(h->stream));
         cudaFree(h->xbuf);
@@ -581,8 +592,9 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
     }
     char *base = (char *)h->xbuf;
     unsigned long long *counter = (unsigned long long *)base;
-    CrossInst *dinst = (CrossInst *)(base + 64);
-    CrossSet *dsets = (CrossSet *)(base + 64 + sizeof(CrossInst) * n_inst);
+    int *dbad = (int *)(base + 64);
+    CrossInst *dinst = (CrossInst *)(base + off_inst);
+    CrossSet *dsets = (CrossSet *)(base + off_sets);
     // pageable sources: each copy returns once the data is staged
     CK(h, cudaMemcpyAsync(dinst, ci.data(), sizeof(CrossInst) * n_inst, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(dsets, cs.data(), sizeof(CrossSet) * n_sets, cudaMemcpyHostToDevice, h->stream));
@@ -596,8 +608,10 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
     a.eps = h->p.eps_weno;
     a.counter = counter;
     a.status = &h->ctl->status;
+    a.bad = dbad;
+    a.vecs = base + off_vecs;
     a.fp64 = (flags & WENO_CROSS_FP64_CHECK) ? 1 : 0;
-    CK(h, launch(h, 7, h->stream, [&] { return launch_cross(a, h->stream); }));
+    CK(h, launch(h, 7, h->stream, [&] { return launch_cross(a, h->stream); }, 2));
     return WENO_OK;
 }
 

@@ -66,6 +66,8 @@ struct CrossSet {
     const int *right;
     void *out;
     long long work_begin;  // first work item of this set (prefix sum)
+    int nsl, nsr;          // shifted copies stored per left / right vector (7 or 1)
+    long long lvec_off, rvec_off;  // element offsets of the set's vectors in CrossArgs::vecs
 };
 
 struct CrossArgs {
@@ -76,10 +78,13 @@ struct CrossArgs {
     double gamma, eps;
     unsigned long long *counter;
     int *status;           // ST_BADINDEX is latched here
+    int *bad;              // per set: an index set held an out-of-range index
+    void *vecs;            // contracted left/right vectors (float or double)
     int fp64;
 };
 
 cudaError_t launch_cross(const CrossArgs &a, cudaStream_t s);
 int cross_max_rank();
+int cross_vec_len();
 
 }  // namespace wg
