@@ -389,8 +389,8 @@ def main():
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
            "api": "weno_run_host (pinned host state, one step per call)"}
 
-    acc = accuracy(weno, I, torch) if rank == 0 else None
     cross = bench_cross(weno, I, torch) if (rank == 0 and not args.no_cross) else None
+    acc = accuracy(weno, I, torch) if rank == 0 else None
     rl = roofline(w, True, kms, kn, cells)
     rl64 = roofline(w, False, kms64, kn64, cells)
     step_tflops = value * 1e6 * flops_cell_stage(w["dim"]) / 1e12 / world

@@ -29,7 +29,7 @@ namespace wg {
 
 constexpr int XT = 256;       // threads per CTA
 constexpr int VP = 32;        // padded vector length (largest rank)
-constexpr int CS = VP + 1;    // shared-memory row stride (odd: lanes on different rows hit different banks)
+constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 consecutive rows hit distinct banks
 constexpr int CH = 64;        // samples per chunk
 constexpr int CP = CH + 6;    // chunk points including the stencil halo
 
@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
         const int rl = mode == 0 ? 1 : in.r[mode - 1];
         const int rr = mode == 2 ? 1 : in.r[mode];
         const int clen = role == 2 ? rr : rl;                    // length of a contracted row
+        const int cl4 = (clen + 3) & ~3;
         const long long nvar = role == 2 ? S.n_right : S.n_left;
         const T *var = vecs + (role == 2 ? S.rvec_off : S.lvec_off);  // the varying side's vectors
         const int nsv = role == 2 ? S.nsr : S.nsl;
@@ -198,20 +199,27 @@ __global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
             const int np = role == 1 ? cn + 6 : cn;
             // chunk reference row (FP32, stencil along the fiber): G(i0) . R
             if (!F64 && role == 1) {
-                for (int u = threadIdx.x; u < 5 * clen; u += XT) {
-                    const int f = u / clen, x = u - f * clen;
-                    const float *g = in.core[f][mode] + ((long long)i0 * rl + x) * rr;
+                for (int u = threadIdx.x; u < 5 * cl4; u += XT) {
+                    const int f = u / cl4, x = u - f * cl4;
                     T acc = T(0);
-                    for (int y = 0; y < rr; ++y) acc += cvtf<T>(__ldg(g + y)) * fixv[f * CS + y];
+                    if (x < clen) {
+                        const float *g = in.core[f][mode] + ((long long)i0 * rl + x) * rr;
+                        for (int y = 0; y < rr; ++y) acc += cvtf<T>(__ldg(g + y)) * fixv[f * CS + y];
+                    }
                     Cref[f * CS + x] = acc;
                 }
                 __syncthreads();
             }
             // contracted rows: role 0/1: C[p][a] = G(p)[a][:] . R ; role 2: C[p][b] = L . G(p)[:][b]
-            for (int u = threadIdx.x; u < 5 * np * clen; u += XT) {
-                const int f = u / (np * clen);
-                const int rem = u - f * np * clen;
-                const int pp = rem / clen, x = rem - pp * clen;
+            // (rows zero-padded to a multiple of 4 entries for the float4 reads below)
+            for (int u = threadIdx.x; u < 5 * np * cl4; u += XT) {
+                const int f = u / (np * cl4);
+                const int rem = u - f * np * cl4;
+                const int pp = rem / cl4, x = rem - pp * cl4;
+                if (x >= clen) {
+                    C[(f * CP + pp) * CS + x] = T(0);
+                    continue;
+                }
                 bool flip = false;
                 int c = p0 + pp;
                 if (role == 1) c = xmap(in, fd, c, flip);
@@ -246,11 +254,23 @@ __global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
                     if (role == 1) {  // the same vector against the 7 rows i-3..i+3
                         const T *lv = var + (v * nsv) * 5 * VP + f * VP;
                         T racc = T(0);
-                        for (int x = 0; x < clen; ++x) {
-                            const T lx = lv[x];
+                        if constexpr (F64) {
+                            for (int x = 0; x < clen; ++x) {
+                                const T lx = lv[x];
 #pragma unroll
-                            for (int k = 0; k < 7; ++k) acc[k] += lx * C[(f * CP + ii + k) * CS + x];
-                            if (!F64) racc += lx * Cref[f * CS + x];
+                                for (int k = 0; k < 7; ++k) acc[k] += lx * C[(f * CP + ii + k) * CS + x];
+                            }
+                        } else {
+                            for (int x = 0; x < cl4; x += 4) {
+                                const float4 l4 = *reinterpret_cast<const float4 *>(lv + x);
+#pragma unroll
+                                for (int k = 0; k < 7; ++k) {
+                                    const float4 c4 = *reinterpret_cast<const float4 *>(C + (f * CP + ii + k) * CS + x);
+                                    acc[k] = fmaf(l4.x, c4.x, fmaf(l4.y, c4.y, fmaf(l4.z, c4.z, fmaf(l4.w, c4.w, acc[k]))));
+                                }
+                                const float4 r4 = *reinterpret_cast<const float4 *>(Cref + f * CS + x);
+                                racc = fmaf(l4.x, r4.x, fmaf(l4.y, r4.y, fmaf(l4.z, r4.z, fmaf(l4.w, r4.w, racc))));
+                            }
                         }
                         ctr[f] = racc;
 #pragma unroll
@@ -258,10 +278,21 @@ __global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
                     } else {          // the 7 shifted vectors against the row of sample i
                         const T *vv = var + (v * 7) * 5 * VP + f * VP;
                         const T *crow = C + (f * CP + ii) * CS;
-                        for (int x = 0; x < clen; ++x) {
-                            const T cx = crow[x];
+                        if constexpr (F64) {
+                            for (int x = 0; x < clen; ++x) {
+                                const T cx = crow[x];
 #pragma unroll
-                            for (int k = 0; k < 7; ++k) acc[k] += vv[k * 5 * VP + x] * cx;
+                                for (int k = 0; k < 7; ++k) acc[k] += vv[k * 5 * VP + x] * cx;
+                            }
+                        } else {
+                            for (int x = 0; x < cl4; x += 4) {
+                                const float4 c4 = *reinterpret_cast<const float4 *>(crow + x);
+#pragma unroll
+                                for (int k = 0; k < 7; ++k) {
+                                    const float4 w4 = *reinterpret_cast<const float4 *>(vv + k * 5 * VP + x);
+                                    acc[k] = fmaf(w4.x, c4.x, fmaf(w4.y, c4.y, fmaf(w4.z, c4.z, fmaf(w4.w, c4.w, acc[k]))));
+                                }
+                            }
                         }
                         ctr[f] = acc[3];
 #pragma unroll

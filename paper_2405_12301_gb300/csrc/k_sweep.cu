@@ -257,8 +257,8 @@ static cudaError_t attr_t()
                                 (int)L::bytes);
 }
 
-// 1D grids, and the z direction of 3D grids (x and y run in the fused k_xy kernel).
-#define WG_SWEEP_TABLE(X, B) X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE) X(3, 2, B, EPI_RHS) X(3, 2, B, EPI_STAGE)
+// 1D grids (2D and 3D grids run in the fused k_xy and k_z kernels).
+#define WG_SWEEP_TABLE(X, B) X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE)
 
 cudaError_t sweep_set_attributes()
 {

@@ -287,7 +287,7 @@ static bool bulk(const weno_ctx *h) { return h->p.precision == WENO_FP32_BULK; }
 
 // One residual evaluation; the last kernel runs epilogue `last`.
 //   1D: the x sweep.  2D: the fused x+y tile kernel.  3D: the fused x+y kernel
-//   per z-plane (stores), then the z sweep (adds, and runs `last`).
+//   per z-plane (stores), then the z kernel (adds, and runs `last`).
 static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
 {
     if (h->dim == 1) {
@@ -296,7 +296,7 @@ static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
         CK(h, launch(h, 4, s, [&] { return launch_xy(2, bulk(h), last, a, s); }));
     } else {
         CK(h, launch(h, 2, s, [&] { return launch_xy(3, bulk(h), EPI_STORE, a, s); }));
-        CK(h, launch(h, 5, s, [&] { return launch_sweep(3, 2, bulk(h), last, a, s); }));
+        CK(h, launch(h, 5, s, [&] { return launch_z(bulk(h), last, a, s); }));
     }
     return WENO_OK;
 }

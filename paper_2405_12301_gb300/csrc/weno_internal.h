@@ -37,6 +37,8 @@ cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &
 cudaError_t sweep_set_attributes();
 // Fused x+y residual of a 2D grid (EPI_RHS / EPI_STAGE) or of the z-planes of a 3D grid (EPI_STORE).
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
+// z direction of a 3D grid, adding the accumulator and ending the residual (EPI_RHS / EPI_STAGE).
+cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 
 cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
                          cudaStream_t s);
