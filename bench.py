@@ -47,6 +47,29 @@ def flops_cell_stage(D):
     return sum(flops_sweep(D, d == D - 1) for d in range(D))
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the ncu summaries under profiles/,
+    or None when no summary records it or the kernel's sources changed since
+    the capture (sha256 prefixes of the listed files must all match)."""
+    import glob
+    import hashlib
+    import re
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            m = re.match(r"traffic_bytes_per_launch: (\d+) kernel: (\S+) sources: (.*)$", line.strip())
+            if not m or m.group(2) != kernel:
+                continue
+            ok = True
+            for item in m.group(3).split():
+                rel, want = item.split("=")
+                f = os.path.join(ROOT, "paper_2405_12301_gb300", rel)
+                if not os.path.exists(f) or hashlib.sha256(open(f, "rb").read()).hexdigest()[:16] != want:
+                    ok = False
+            if ok:
+                return int(m.group(1))
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -240,11 +263,30 @@ def roofline(w, prec_bulk, kms, kn, cells):
     achieved = flops / (per_launch_ms * 1e-3) / 1e12
     peak = PEAK_FP32_TFLOPS if prec_bulk else PEAK_FP64_TFLOPS
     names = KIND_NAMES
+    traffic = recorded_traffic(names[k]) if prec_bulk and w["name"] == WORKLOADS["2d"]["name"] else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": names[k], "ms_per_launch": per_launch_ms,
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "kernel": names[k], "ms_per_launch": per_launch_ms,
             "pipe": "fp32" if prec_bulk else "fp64",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if prec_bulk
             else "nominal GB300 FP64 1.25 TFLOP/s"}
+
+
+def max_over_ranks(v, dist, device="cuda"):
+    """The largest value of v over all ranks (the slowest rank's time); v itself
+    without torch.distributed."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, seconds):
+    """Whole-job throughput in millions of units per second: every rank runs its
+    own replica, and the job takes as long as its slowest rank."""
+    return units_per_rank * world / seconds / 1e6
 
 
 KIND_NAMES = ["unused0", "unused1", "xy_plane_3d", "sweep_x_1d", "xy_fused_2d", "sweep_z_3d", "alpha", "small"]
@@ -360,16 +402,12 @@ def main():
     clk = clocks.stop()
 
     def mx(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, dist)
 
     ms, ms64 = mx(ms), mx(ms64)
-    value = cells * 3 * args.steps * world / (ms * 1e-3) / 1e6
+    value = job_value(cells * 3 * args.steps, world, ms * 1e-3)
     steps64 = max(3, args.steps // 4)
-    value64 = cells * 3 * steps64 * world / (ms64 * 1e-3) / 1e6
+    value64 = job_value(cells * 3 * steps64, world, ms64 * 1e-3)
 
     # end to end through the C ABI with host buffers: every step copies the
     # state in from pinned host memory, steps, and copies it back
@@ -385,7 +423,7 @@ def main():
     e2e_s = mx(time.perf_counter() - t0)
     s.close()
     state_bytes = Uh.numel() * 8
-    e2e = {"value": cells * 3 * args.steps * world / e2e_s / 1e6, "unit": "Mcell-stage/s",
+    e2e = {"value": job_value(cells * 3 * args.steps, world, e2e_s), "unit": "Mcell-stage/s",
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
            "api": "weno_run_host (pinned host state, one step per call)"}
 

@@ -297,233 +297,6 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     }
 }
 
-// ---------------------------------------------------------------------------
-// z direction of a 3D grid, ending the residual: a CTA owns 32 x-cells x TZ = 8
-// z-cells of one y-row, one cell per thread, plus the 3 + 3 halo z-planes of
-// its 32 columns.  Same phases as above for one direction; the epilogue adds
-// the x+y part left in the accumulator by k_xy<3, ..., EPI_STORE>, then writes
-// L(U) or applies the SSP-RK3 stage combination and publishes the wavespeed max.
-namespace zs {
-constexpr int NT = 256;
-constexpr int TX = 32, TZ = 8;
-constexpr int BZ = TZ + 6;                  // column extent with halo
-constexpr int NZP = TX * BZ;                // z-flux points: 32 x 14
-constexpr int NZI = TX * (TZ + 1);          // z interfaces: 32 x 9
-constexpr int NHALO = 6 * TX;               // 192 halo points
-
-template <bool BULK> struct Layout {
-    using T = typename std::conditional<BULK, float, double>::type;
-    static constexpr int NF = 5;
-    static constexpr size_t F_off = 0;
-    static constexpr size_t fz_off = (sizeof(T) * NF * NZI + 15) & ~size_t(15);
-    static constexpr size_t ref_off = (fz_off + sizeof(T) * 2 * NF * NZP + 15) & ~size_t(15);
-    static constexpr size_t bytes = ref_off + sizeof(RefState<3>);
-};
-}  // namespace zs
-
-template <bool BULK, int EPI>
-__global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
-{
-    using namespace zs;
-    using L = Layout<BULK>;
-    using T = typename L::T;
-    constexpr int NF = 5;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *Fz = reinterpret_cast<T *>(smem + L::F_off);        // [NF][TZ+1][TX]
-    T *fz = reinterpret_cast<T *>(smem + L::fz_off);       // [2][NF][BZ][TX]
-    RefState<3> &ref = *reinterpret_cast<RefState<3> *>(smem + L::ref_off);
-
-    const long long dtbits = __double_as_longlong(a.ctl->dt);
-    if (a.check_dt && dtbits == 0) return;
-    const double dt = __longlong_as_double(dtbits);
-    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
-
-    const int nx = a.n[0], nz = a.n[2];
-    const long long N = a.N, sz = a.stride[2];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.z * TZ;
-    const long long yoff = (long long)blockIdx.y * a.stride[1];
-    const int tx = threadIdx.x & 31, tz = threadIdx.x >> 5;
-    const int gx = x0 + tx, gz = z0 + tz;
-    const bool own = gx < nx && gz < nz;
-    const long long cell = yoff + (long long)(gz < nz ? gz : nz - 1) * sz + (gx < nx ? gx : nx - 1);
-
-    double un[NF];
-    if (EPI == EPI_STAGE && a.stage > 0) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
-    }
-    if (BULK) {
-        if (threadIdx.x < 32) {
-            const long long c0 = yoff + (long long)(z0 < nz ? z0 : nz - 1) * sz + (x0 < nx ? x0 : nx - 1);
-            double q[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
-            RefState<3> r;
-            make_ref<3>(q, a.gm1_f, r);
-            if (threadIdx.x == 0) ref = r;
-        }
-        __syncthreads();
-    }
-    const T al = BULK ? (T)f64_to_f32(alpha) : (T)alpha;
-    const double gm1 = a.gamma - 1.0;
-    const bool interior = z0 >= 3 && z0 + TZ + 3 <= nz && x0 + TX <= nx;
-
-    auto load_point = [&](int lx, int lz, double *q) {
-        int cx = x0 + lx, cz = z0 + lz;
-        bool fz_ = false;
-        if (!interior) {
-            cx = cx < nx ? cx : nx - 1;  // columns beyond the grid only feed cells that are not written
-            cz = cz < nz + 2 ? cz : nz + 2;
-            cz = ghost_source(cz, nz, a.bc[2][0], a.bc[2][1], fz_);
-        }
-        const double *src = a.U + yoff + (long long)cz * sz + cx;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) q[f] = __ldg(src + f * N);
-        if (fz_) q[3] = -q[3];
-    };
-    auto flux_store = [&](const T *q, int lx, int lz) {
-        T fp[NF], fm[NF];
-        if constexpr (BULK) split_flux_diff<3, 2>(q, ref, al, a.gm1_f, fp, fm);
-        else split_flux_f64<3, 2>(q, al, gm1, fp, fm);
-        const int o = (lz + 3) * TX + lx;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            fz[f * NZP + o] = fp[f];
-            fz[(NF + f) * NZP + o] = fm[f];
-        }
-    };
-
-    double uk[NF];
-    float hk[NF], lk[NF];
-    load_point(tx, tz, uk);
-    {
-        T q[NF];
-        if constexpr (BULK) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                split_f64(uk[f], hk[f], lk[f]);
-                q[f] = (hk[f] - ref.hi[f]) + (lk[f] - ref.lo[f]);
-            }
-        } else {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = uk[f];
-        }
-        flux_store(q, tx, tz);
-    }
-    if (threadIdx.x < NHALO) {
-        const int lx = threadIdx.x & 31, k = threadIdx.x >> 5;
-        const int lz = k < 3 ? k - 3 : TZ + k - 3;
-        double qd[NF];
-        load_point(lx, lz, qd);
-        T q[NF];
-        if constexpr (BULK) diff_from_ref<3>(qd, ref, q);
-        else {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = qd[f];
-        }
-        flux_store(q, lx, lz);
-    }
-    __syncthreads();
-
-    const T eps = BULK ? (T)a.eps_f : (T)a.eps;
-    auto face_z = [&](int f, int lx, int j) -> T {  // between local planes j-1 and j of column lx
-        const T *P = fz + f * NZP + lx;
-        const T *M = fz + (NF + f) * NZP + lx;
-        return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
-               weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
-    };
-    T fzb[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        fzb[f] = face_z(f, tx, tz);
-        Fz[f * NZI + tz * TX + tx] = fzb[f];
-    }
-    if (threadIdx.x < NF * TX) {
-        const int f = threadIdx.x >> 5, lx = threadIdx.x & 31;
-        Fz[f * NZI + TZ * TX + lx] = face_z(f, lx, TZ);
-    }
-    __syncthreads();
-
-    const T ihz = BULK ? (T)a.inv_h_f[2] : (T)a.inv_h[2];
-    const T *acc = reinterpret_cast<const T *>(a.acc);
-    T r[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        const T dz = Fz[f * NZI + (tz + 1) * TX + tx] - fzb[f];
-        r[f] = acc[f * N + cell] + (-dz * ihz);
-    }
-    if (EPI == EPI_RHS) {
-        if (own) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                if constexpr (BULK) a.Rout[f * N + cell] = f32_to_f64(r[f]);
-                else a.Rout[f * N + cell] = r[f];
-            }
-        }
-        return;
-    }
-    if constexpr (BULK) {
-        float s = 0.0f;
-        bool bad = false;
-        if (own) {
-            const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
-            float qn[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                float dl = bdt * r[f];
-                if (a.stage > 0) {
-                    float hn, ln;
-                    split_f64(un[f], hn, ln);
-                    dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
-                }
-                a.Uout[f * N + cell] = uk[f] + f32_to_f64(dl);
-                qn[f] = hk[f] + (lk[f] + dl);
-            }
-            s = wavespeed_f32<3>(qn, a.gamma_f, bad);
-        }
-        block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-    } else {
-        double cmax = 0.0;
-        bool bad = false;
-        if (own) {
-            const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
-            const double bn = a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0);
-            double out[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const double sf = uk[f] + dt * r[f];
-                out[f] = a.stage == 0 ? sf : an * un[f] + bn * sf;
-                a.Uout[f * N + cell] = out[f];
-            }
-            cmax = wavespeed_f64<3>(out, a.gamma, bad);
-        }
-        block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-    }
-}
-
-template <bool BULK, int EPI>
-static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
-{
-    using L = zs::Layout<BULK>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    dim3 grid((unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1], (unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ));
-    k_z<BULK, EPI><<<grid, zs::NT, L::bytes, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
-{
-    if (bulk) return epi == EPI_STAGE ? launch_z_t<true, EPI_STAGE>(a, s) : launch_z_t<true, EPI_RHS>(a, s);
-    return epi == EPI_STAGE ? launch_z_t<false, EPI_STAGE>(a, s) : launch_z_t<false, EPI_RHS>(a, s);
-}
-
 template <int D, bool BULK, int EPI>
 static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
 {
