@@ -50,8 +50,10 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
 
     const int nx = a.n[0], nz = a.n[2];
     const long long N = a.N, sz = a.stride[2];
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.z * TZ;
-    const long long yoff = (long long)blockIdx.y * a.stride[1];
+    // z-tiles are the fastest grid index, so that tiles sharing halo planes run
+    // close together and find those planes in L2
+    const int x0 = blockIdx.y * TX, z0 = blockIdx.x * TZ;
+    const long long yoff = (long long)blockIdx.z * a.stride[1];
     const int tx = threadIdx.x & 31, tz = threadIdx.x >> 5;
     const int gx = x0 + tx, gz = z0 + tz;
     const bool own = gx < nx && gz < nz;
@@ -223,7 +225,7 @@ static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1], (unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ));
+    dim3 grid((unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ), (unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1]);
     k_z<BULK, EPI><<<grid, zs::NT, L::bytes, s>>>(a);
     return cudaGetLastError();
 }

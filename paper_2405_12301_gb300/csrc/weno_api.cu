@@ -186,9 +186,10 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
             h->h[d] = d < grid->dim ? (grid->hi[d] - grid->lo[d]) / (double)nd : 1.0;
             h->N *= nd;
         }
-        if (h->n[1] > 65535 * 2 || h->n[2] > 65535) {
+        // launch-grid limits (y and z grid dimensions hold at most 65535 blocks)
+        if ((h->dim == 2 && h->n[1] > 65535ll * 8) || (h->dim == 3 && (h->n[1] > 65535 || h->n[2] > 65535))) {
             delete h;
-            return fail(nullptr, WENO_ERR_ARG, "weno_init: ny <= 131070 and nz <= 65535 required");
+            return fail(nullptr, WENO_ERR_ARG, "weno_init: need ny <= 524280 (2D), ny, nz <= 65535 (3D)");
         }
     }
     static bool attrs = false;
