@@ -65,10 +65,12 @@ typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_TRANSMISSIVE = 1, WENO_BC_REFLECTIV
  * the state, its stage combination and the conservation sums stay FP64. */
 typedef enum { WENO_FP64 = 0, WENO_FP32_BULK = 1 } weno_precision;
 
-/* Lax-Friedrichs constant: one global alpha = max over cells of |u| + a
- * (Sec. 4.3, Eq. cfl-other).  WENO_ALPHA_PER_DIR (max |u_d| + a per
- * direction, Eq. lax-friedrichs read per direction) is declared for the
- * interface but returns WENO_ERR_UNSUPPORTED. */
+/* Lax-Friedrichs constant.  WENO_ALPHA_GLOBAL_NORM: one global alpha = max
+ * over cells of |u| + a, used by every direction (Sec. 4.3, Eq. cfl-other).
+ * WENO_ALPHA_PER_DIR: direction d splits with alpha_d = max over cells of
+ * |u_d| + a (Eq. lax-friedrichs, alpha = max |f'(u)| read per direction).
+ * Either way both are recomputed from every stage's state, and dt uses the
+ * global max(|u| + a). */
 typedef enum { WENO_ALPHA_GLOBAL_NORM = 0, WENO_ALPHA_PER_DIR = 1 } weno_alpha_mode;
 
 typedef struct {
@@ -102,7 +104,9 @@ int weno_destroy(weno_handle h);
 int weno_set_stream(weno_handle h, void *cuda_stream);
 
 /* alpha_dev[0] = max over interior cells of |u| + sqrt(gamma p / rho) of U
- * (Sec. 4.3), computed in the handle's precision.  alpha_dev: device double. */
+ * (Sec. 4.3), computed in the handle's precision.  alpha_dev: device double.
+ * (In WENO_ALPHA_PER_DIR mode the splitting constants are per direction; this
+ * call still returns the global maximum, the one dt uses.) */
 int weno_alpha(weno_handle h, const double *U, double *alpha_dev);
 
 /* R = L(U) (Sec. 4.1, Eq. euler-system-for-loop), with alpha recomputed from U.

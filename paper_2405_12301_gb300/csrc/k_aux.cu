@@ -9,11 +9,13 @@ namespace wg {
 
 template <int D, bool BULK>
 __global__ void __launch_bounds__(256) k_alpha(const double *__restrict__ U, long long N, double gamma, Ctl *ctl,
-                                               int slot)
+                                               int slot, int per_dir)
 {
     constexpr int NF = D + 2;
-    double m = 0.0;
-    float mf = 0.0f;
+    double m = 0.0, md[D];
+    float mf = 0.0f, mdf[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) { md[e] = 0.0; mdf[e] = 0.0f; }
     bool bad = false;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         double q[NF];
@@ -25,16 +27,40 @@ __global__ void __launch_bounds__(256) k_alpha(const double *__restrict__ U, lon
 #pragma unroll
             for (int f = 0; f < NF; ++f) qf[f] = f64_to_f32(q[f]);
             mf = fmaxf(mf, wavespeed_f32<D>(qf, (float)gamma, b));
+            if (per_dir) {
+                float sd[D];
+                dirspeeds_f32<D>(qf, (float)gamma, sd);
+#pragma unroll
+                for (int e = 0; e < D; ++e) mdf[e] = fmaxf(mdf[e], b ? 0.0f : sd[e]);
+            }
         } else {
             m = fmax(m, wavespeed_f64<D>(q, gamma, b));
+            if (per_dir) {
+                double sd[D];
+                dirspeeds_f64<D>(q, gamma, sd);
+#pragma unroll
+                for (int e = 0; e < D; ++e) md[e] = fmax(md[e], b ? 0.0 : sd[e]);
+            }
         }
         bad |= b;
     }
-    if (BULK) m = (double)mf;
+    if (BULK) {
+        m = (double)mf;
+#pragma unroll
+        for (int e = 0; e < D; ++e) md[e] = (double)mdf[e];
+    }
     block_max_publish(m, bad, &ctl->alpha[slot], &ctl->status);
+    if (per_dir) {
+#pragma unroll
+        for (int e = 0; e < D; ++e) block_max_publish(md[e], false, &ctl->alpha_dir[slot][e], &ctl->status);
+    }
 }
 
-__global__ void k_reset_slot(Ctl *ctl, int slot) { ctl->alpha[slot] = 0ull; }
+__global__ void k_reset_slot(Ctl *ctl, int slot)
+{
+    ctl->alpha[slot] = 0ull;
+    for (int e = 0; e < 3; ++e) ctl->alpha_dir[slot][e] = 0ull;
+}
 
 __global__ void k_copy_alpha(const Ctl *ctl, int slot, double *out)
 {
@@ -63,9 +89,10 @@ __global__ void k_step_begin(Ctl *c)
     }
     c->dt = dt;
     c->t_next = tn;
-    c->alpha[1] = 0ull;
-    c->alpha[2] = 0ull;
-    c->alpha[3] = 0ull;
+    for (int k = 1; k < 4; ++k) {
+        c->alpha[k] = 0ull;
+        for (int e = 0; e < 3; ++e) c->alpha_dir[k][e] = 0ull;
+    }
 }
 
 // End of a step: advance the time and carry alpha(U^{n+1}) into slot 0.
@@ -75,6 +102,7 @@ __global__ void k_step_end(Ctl *c)
         c->t = c->t_next;
         c->steps += 1;
         c->alpha[0] = c->alpha[3];
+        for (int e = 0; e < 3; ++e) c->alpha_dir[0][e] = c->alpha_dir[3][e];
     }
 }
 
@@ -136,13 +164,13 @@ cudaError_t launch_sums(const double *U, int nf, long long N, double *partials, 
 }
 
 cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
-                         cudaStream_t s)
+                         int per_dir, cudaStream_t s)
 {
     int blocks = (int)((N + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
 #define X(D, B) \
-    if (dim == D && bulk == B) k_alpha<D, B><<<blocks, 256, 0, s>>>(U, N, gamma, ctl, slot);
+    if (dim == D && bulk == B) k_alpha<D, B><<<blocks, 256, 0, s>>>(U, N, gamma, ctl, slot, per_dir);
     X(1, false) X(2, false) X(3, false) X(1, true) X(2, true) X(3, true)
 #undef X
     return cudaGetLastError();

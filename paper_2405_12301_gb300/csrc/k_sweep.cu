@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
         return x < a.n[0];
     };
 
-    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    const double alpha = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][DIR])
+                                   : __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     const float alpha_f = BULK ? f64_to_f32(alpha) : 0.0f;  // integer pipe: cvt issues at FP64 rate
     const double gm1 = a.gamma - 1.0;
     const T eps = BULK ? (T)a.eps_f : (T)a.eps;
@@ -232,6 +233,8 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     if (EPI == EPI_STAGE) {
         if (BULK) cmax = (double)cmaxf;
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+        // 1D: |u_x| + a equals |u| + a, so the x slot takes the same maximum
+        if (a.per_dir) block_max_publish(cmax, false, &a.ctl->alpha_dir[a.slot_out][0], &a.ctl->status);
     }
 }
 

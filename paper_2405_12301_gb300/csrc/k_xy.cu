@@ -68,6 +68,9 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    // LF constants of the x and y splittings: the global alpha, or per direction
+    const double alx = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha;
+    const double aly = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha;
 
     const int nx = a.n[0], ny = a.n[1];
     const long long N = a.N;
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
         }
         __syncthreads();
     }
-    const T al = BULK ? (T)f64_to_f32(alpha) : (T)alpha;
+    const T alX = BULK ? (T)f64_to_f32(alx) : (T)alx;
+    const T alY = BULK ? (T)f64_to_f32(aly) : (T)aly;
     const double gm1 = a.gamma - 1.0;
     // interior tiles (halo inside the grid) skip the boundary rule
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
@@ -122,11 +126,11 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
         T fp[NF], fm[NF];
         if constexpr (BULK) {
-            if (dirx) split_flux_diff<D, 0>(q, ref, al, a.gm1_f, fp, fm);
-            else split_flux_diff<D, 1>(q, ref, al, a.gm1_f, fp, fm);
+            if (dirx) split_flux_diff<D, 0>(q, ref, alX, a.gm1_f, fp, fm);
+            else split_flux_diff<D, 1>(q, ref, alY, a.gm1_f, fp, fm);
         } else {
-            if (dirx) split_flux_f64<D, 0>(q, al, gm1, fp, fm);
-            else split_flux_f64<D, 1>(q, al, gm1, fp, fm);
+            if (dirx) split_flux_f64<D, 0>(q, alX, gm1, fp, fm);
+            else split_flux_f64<D, 1>(q, alY, gm1, fp, fm);
         }
         if (dirx) {
             const int o = ly * BX + (lx + 3);
@@ -258,7 +262,9 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     // EPI_STAGE: U' = a_n U^n + b_n (U^k + dt R)
     if constexpr (BULK) {
         // U' = U^k + D, D = a_n (U^n - U^k) + b_n dt R in FP32 from hi/lo differences
-        float s = 0.0f;
+        float s = 0.0f, sd[D];
+#pragma unroll
+        for (int e = 0; e < D; ++e) sd[e] = 0.0f;
         bool bad = false;
         if (own) {
             const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
@@ -276,10 +282,17 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<D>(qn, a.gamma_f, bad);
+            if (a.per_dir && !bad) dirspeeds_f32<D>(qn, a.gamma_f, sd);
         }
         block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+        if (a.per_dir) {
+#pragma unroll
+            for (int e = 0; e < D; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
+        }
     } else {
-        double cmax = 0.0;
+        double cmax = 0.0, sd[D];
+#pragma unroll
+        for (int e = 0; e < D; ++e) sd[e] = 0.0;
         bool bad = false;
         if (own) {
             const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
@@ -292,8 +305,13 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                 a.Uout[f * N + cell] = out[f];
             }
             cmax = wavespeed_f64<D>(out, a.gamma, bad);
+            if (a.per_dir && !bad) dirspeeds_f64<D>(out, a.gamma, sd);
         }
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+        if (a.per_dir) {
+#pragma unroll
+            for (int e = 0; e < D; ++e) block_max_publish(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
+        }
     }
 }
 

@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
-    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    const double alpha = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][2])
+                                   : __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
 
     const int nx = a.n[0], nz = a.n[2];
     const long long N = a.N, sz = a.stride[2];
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         return;
     }
     if constexpr (BULK) {
-        float s = 0.0f;
+        float s = 0.0f, sd[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
         if (own) {
             const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
@@ -193,10 +194,15 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
+            if (a.per_dir && !bad) dirspeeds_f32<3>(qn, a.gamma_f, sd);
         }
         block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+        if (a.per_dir) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
+        }
     } else {
-        double cmax = 0.0;
+        double cmax = 0.0, sd[3] = {0.0, 0.0, 0.0};
         bool bad = false;
         if (own) {
             const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
@@ -209,8 +215,13 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
                 a.Uout[f * N + cell] = out[f];
             }
             cmax = wavespeed_f64<3>(out, a.gamma, bad);
+            if (a.per_dir && !bad) dirspeeds_f64<3>(out, a.gamma, sd);
         }
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+        if (a.per_dir) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) block_max_publish(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
+        }
     }
 }
 

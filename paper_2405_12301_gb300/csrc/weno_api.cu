@@ -155,9 +155,8 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
         return fail(nullptr, WENO_ERR_ARG, "weno_init: need gamma > 1, eps_weno > 0, cfl >= 0");
     if (p.precision != WENO_FP64 && p.precision != WENO_FP32_BULK)
         return fail(nullptr, WENO_ERR_ARG, "weno_init: bad precision");
-    if (p.alpha_mode == WENO_ALPHA_PER_DIR)
-        return fail(nullptr, WENO_ERR_UNSUPPORTED, "weno_init: per-direction alpha is not implemented on the GPU");
-    if (p.alpha_mode != WENO_ALPHA_GLOBAL_NORM) return fail(nullptr, WENO_ERR_ARG, "weno_init: bad alpha_mode");
+    if (p.alpha_mode != WENO_ALPHA_GLOBAL_NORM && p.alpha_mode != WENO_ALPHA_PER_DIR)
+        return fail(nullptr, WENO_ERR_ARG, "weno_init: bad alpha_mode");
     for (int d = 0; d < 3; ++d)
         for (int s = 0; s < 2; ++s)
             if (p.bc[d][s] < 0 || p.bc[d][s] > 2) return fail(nullptr, WENO_ERR_ARG, "weno_init: bad boundary rule");
@@ -281,6 +280,7 @@ static SweepArgs base_args(weno_ctx *h)
     a.eps_f = (float)h->p.eps_weno;
     for (int d = 0; d < 3; ++d) a.inv_h_f[d] = (float)a.inv_h[d];
     a.acc = h->acc;
+    a.per_dir = h->p.alpha_mode == WENO_ALPHA_PER_DIR ? 1 : 0;
     return a;
 }
 
@@ -328,7 +328,10 @@ static int enqueue_step(weno_ctx *h, double *U, cudaStream_t s)
 static int enqueue_alpha0(weno_ctx *h, const double *U, cudaStream_t s)
 {
     CK(h, launch(h, 7, s, [&] { return launch_reset_slot(h->ctl, 0, s); }));
-    CK(h, launch(h, 6, s, [&] { return launch_alpha(h->dim, bulk(h), U, h->N, h->p.gamma, h->ctl, 0, s); }));
+    CK(h, launch(h, 6, s, [&] {
+           return launch_alpha(h->dim, bulk(h), U, h->N, h->p.gamma, h->ctl, 0,
+                               h->p.alpha_mode == WENO_ALPHA_PER_DIR ? 1 : 0, s);
+       }));
     return WENO_OK;
 }
 

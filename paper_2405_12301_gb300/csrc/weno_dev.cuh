@@ -29,6 +29,7 @@ struct Ctl {
     double dt_req;         // > 0: fixed dt; otherwise CFL
     double cfl_h;          // cfl * min_d h_d
     unsigned long long alpha[4];
+    unsigned long long alpha_dir[4][3];  // per-direction max(|u_d| + a), same slots (per-direction mode)
     long long steps;       // steps taken since the last set_time
     long long max_steps;   // steps bound of the current run call
     int status;            // ST_* bits, latched
@@ -266,6 +267,40 @@ __device__ __forceinline__ double wavespeed_f64(const double *q, double gamma, b
     bad = !(rho > 0.0) || !(p > 0.0) || !isfinite(u2) || !isfinite(q[D + 1]);
     const double a = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
     return bad ? 0.0 : __dadd_rn(__dsqrt_rn(u2), a);
+}
+
+// Per-direction speeds |u_d| + a (FP64, same operation order as the plain formula).
+template <int D>
+__device__ __forceinline__ void dirspeeds_f64(const double *q, double gamma, double *sd)
+{
+    const double rho = q[0];
+    double u2 = 0.0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const double ue = __ddiv_rn(q[1 + e], rho);
+        u2 = __dadd_rn(u2, __dmul_rn(ue, ue));
+    }
+    const double p = __dmul_rn(gamma - 1.0, __dsub_rn(q[D + 1], __dmul_rn(__dmul_rn(0.5, rho), u2)));
+    const double a = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+#pragma unroll
+    for (int e = 0; e < D; ++e) sd[e] = __dadd_rn(fabs(__ddiv_rn(q[1 + e], rho)), a);
+}
+
+template <int D>
+__device__ __forceinline__ void dirspeeds_f32(const float *q, float gamma, float *sd)
+{
+    const float rho = q[0];
+    const float ir = 1.0f / rho;
+    float u2 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const float ue = q[1 + e] * ir;
+        u2 += ue * ue;
+    }
+    const float p = (gamma - 1.0f) * (q[D + 1] - 0.5f * rho * u2);
+    const float a = sqrtf(gamma * p * ir);
+#pragma unroll
+    for (int e = 0; e < D; ++e) sd[e] = fabsf(q[1 + e] * ir) + a;
 }
 
 template <int D>

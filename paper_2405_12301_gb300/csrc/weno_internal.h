@@ -30,6 +30,7 @@ struct SweepArgs {
     int slot_in;         // alpha slot used for the splitting
     int slot_out;        // alpha slot the EPI_STAGE epilogue publishes to
     int check_dt;        // skip all work when ctl->dt == 0
+    int per_dir;         // LF alpha per direction (alpha_dir slots) instead of one global alpha
 };
 
 // Launches the sweep of direction dir for a dim-dimensional grid.
@@ -41,7 +42,7 @@ cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStrea
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 
 cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
-                         cudaStream_t s);
+                         int per_dir, cudaStream_t s);
 cudaError_t launch_reset_slot(Ctl *ctl, int slot, cudaStream_t s);
 cudaError_t launch_step_begin(Ctl *ctl, cudaStream_t s);
 cudaError_t launch_step_end(Ctl *ctl, cudaStream_t s);

@@ -41,5 +41,8 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_ARG
     assert b"gamma" in L.weno_last_error(None)
     p.gamma = 1.4
-    p.alpha_mode = weno.ALPHA_PER_DIR
-    assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_UNSUPPORTED
+    p.alpha_mode = 7  # not a weno_alpha_mode
+    assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_ARG
+    p.alpha_mode = weno.ALPHA_GLOBAL_NORM
+    p.bc[0][1] = 9    # not a weno_bc
+    assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_ARG

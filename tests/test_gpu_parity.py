@@ -49,7 +49,7 @@ def host(t):
 
 def solver(W, cfg, precision=0, cfl=0.5):
     return W.Solver(cfg.dim, cfg.n[:cfg.dim], cfg.lo[:cfg.dim], cfg.hi[:cfg.dim], gamma=cfg.gamma,
-                    eps_weno=cfg.eps, cfl=cfl, bc=cfg.bc, precision=precision)
+                    eps_weno=cfg.eps, cfl=cfl, bc=cfg.bc, precision=precision, alpha_mode=cfg.alpha_mode)
 
 
 def fp64_rhs_tol(cfg, U, Rref, alpha):
@@ -381,3 +381,47 @@ def test_full_size_3d_x_only_field_matches_1d_oracle(W, precision):
     else:
         tol = _variation_tol(cfg3, U3, want, alpha)
     assert (np.abs(Rg - want) <= tol).all()
+
+
+# ------------------------------------------------ per-direction LF constant
+PD_CASES = [
+    (1, (200,), ((P, P),)),
+    (2, (70, 45), ((T, R), (P, P))),
+    (3, (36, 30, 27), ((P, P), (T, T), (R, P))),
+]
+
+
+@pytest.mark.parametrize("dim,n,bc", PD_CASES)
+def test_per_direction_alpha_fp64_matches_oracle(W, dim, n, bc):
+    """alpha_d = max |u_d| + a per direction (Eq. lax-friedrichs read per direction):
+    the residual within the FP64 bound, one step to 1e-12 and a run to 1e-10."""
+    cfg = O.Cfg(dim=dim, n=n, bc=bc, alpha_mode=O.ALPHA_PER_DIR)
+    U = I.random_state(dim, n, seed=400 + sum(n), jumps=True)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    assert (np.abs(host(Rd) - Rref) <= fp64_rhs_tol(cfg, U, Rref, max(aref))).all()
+    Uref = O.ssprk3_step(cfg, U, O.cfl_dt(cfg, U, 0.5))
+    Ud = dev(U)
+    s.set_time(0.0)
+    s.step(Ud, 1e9)
+    assert rel_field_err(host(Ud), Uref) <= 1e-12
+    Uref, steps, t = O.run(cfg, U, 0.03, cfl=0.5)
+    Ud = dev(U)
+    s.set_time(0.0)
+    assert s.run(Ud, 0.03, graph_steps=4) == steps
+    assert rel_field_err(host(Ud), Uref) <= 1e-10
+
+
+def test_per_direction_alpha_bulk_matches_oracle(W):
+    cfg = O.Cfg(dim=2, n=(64, 48), alpha_mode=O.ALPHA_PER_DIR)
+    U = I.random_state(2, (64, 48), seed=410, jumps=True)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg, precision=1)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    assert (np.abs(host(Rd) - Rref) <= _variation_tol(cfg, U, Rref, max(aref))).all()
+    # per-direction splitting must differ from the global one on this state
+    Rg, _ = O.residual(O.Cfg(dim=2, n=(64, 48)), U)
+    assert np.abs(Rg - Rref).max() > 1e3 * np.abs(host(Rd) - Rref).max()
