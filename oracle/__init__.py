@@ -19,7 +19,7 @@ from . import build as _build
 _lib = None
 
 EULER, ADVECT, BURGERS = 0, 1, 2
-PERIODIC, TRANSMISSIVE, REFLECTIVE = 0, 1, 2
+PERIODIC, TRANSMISSIVE, REFLECTIVE, INFLOW = 0, 1, 2, 3
 ALPHA_GLOBAL_NORM, ALPHA_PER_DIR = 0, 1
 
 
@@ -27,7 +27,8 @@ class _OCfg(C.Structure):
     _fields_ = [("dim", C.c_int), ("model", C.c_int), ("n", C.c_int * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("gamma", C.c_double), ("eps", C.c_double),
-                ("bc", (C.c_int * 2) * 3), ("alpha_mode", C.c_int)]
+                ("bc", (C.c_int * 2) * 3), ("alpha_mode", C.c_int),
+                ("bc_state", ((C.c_double * 5) * 2) * 3)]
 
 
 @dataclasses.dataclass
@@ -42,6 +43,7 @@ class Cfg:
     bc: tuple = ((PERIODIC, PERIODIC),) * 3
     alpha_mode: int = ALPHA_GLOBAL_NORM
     model: int = EULER
+    bc_state: object = None   # [3][2][nf] conserved inflow states (INFLOW sides)
 
     @property
     def nf(self):
@@ -68,6 +70,11 @@ class Cfg:
             c.hi[d] = float(self.hi[d]) if d < len(self.hi) else 1.0
             c.bc[d][0], c.bc[d][1] = self.bc[d] if d < len(self.bc) else (PERIODIC, PERIODIC)
         c.gamma, c.eps, c.alpha_mode = self.gamma, self.eps, self.alpha_mode
+        if self.bc_state is not None:
+            for d in range(3):
+                for side in range(2):
+                    for f, v in enumerate(self.bc_state[d][side]):
+                        c.bc_state[d][side][f] = float(v)
         return c
 
 

@@ -31,6 +31,9 @@
  *   - alpha is one global scalar max over interior cells of |u| + a, recomputed
  *     from every stage's state (option: per-direction max of |u_d| + a);
  *   - transmissive boundaries copy the nearest interior cell into the ghosts;
+ *   - inflow boundaries hold a given conserved state in all three ghost layers
+ *     (the full-grid counterpart of the TT inflow rule of Sec. 4.5, which
+ *     zeroes the ghost rows and adds a rank-1 TT of the inflow state);
  *   - the grid is cell-centred: x_i = lo + (i + 1/2) h.
  *
  * Scalar models (linear advection u_t + u_x + u_y + u_z = 0 and Burgers
@@ -46,7 +49,7 @@
 #include <string.h>
 
 enum { M_EULER = 0, M_ADVECT = 1, M_BURGERS = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 enum { ALPHA_GLOBAL_NORM = 0, ALPHA_PER_DIR = 1 };
 
 typedef struct {
@@ -59,6 +62,7 @@ typedef struct {
     double eps;       /* WENO epsilon */
     int bc[3][2];     /* per direction: [low side, high side] */
     int alpha_mode;   /* ALPHA_GLOBAL_NORM or ALPHA_PER_DIR */
+    double bc_state[3][2][5];  /* conserved state of an inflow side (BC_INFLOW) */
 } ocfg;
 
 #define NG 3          /* ghost layers per side, Sec. 4.5 */
@@ -214,10 +218,17 @@ static double *o_pad(const ocfg *c, const double *U, int64_t pn[3])
                 if (outside > 1) continue;
                 int src[3] = {g[0], g[1], g[2]};
                 int flip = 0;
-                if (outside == 1)
-                    src[dout] = o_ghost_source(g[dout], c->n[dout], c->bc[dout][0], c->bc[dout][1], &flip);
-                int64_t s = ((int64_t)src[2] * ny + src[1]) * nx + src[0];
                 int64_t t = (pk * pn[1] + pj) * pn[0] + pi;
+                if (outside == 1) {
+                    /* inflow (Sec. 4.5): the ghost layers hold the given inflow state */
+                    int side = g[dout] < 0 ? 0 : 1;
+                    if (c->bc[dout][side] == BC_INFLOW) {
+                        for (int f = 0; f < nf; ++f) P[(int64_t)f * pcells + t] = c->bc_state[dout][side][f];
+                        continue;
+                    }
+                    src[dout] = o_ghost_source(g[dout], c->n[dout], c->bc[dout][0], c->bc[dout][1], &flip);
+                }
+                int64_t s = ((int64_t)src[2] * ny + src[1]) * nx + src[0];
                 for (int f = 0; f < nf; ++f) {
                     double val = U[(int64_t)f * o_ncells(c) + s];
                     if (flip && c->model == M_EULER && f == 1 + dout) val = -val;

@@ -401,3 +401,36 @@ def test_cross_eval_equals_full_grid_residual(bc):
                         want = Rf[:, ix[2], ix[1], ix[0]]
                         got = out[:, li, i, ri]
                         np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(Rf).max())
+
+
+# ---------------------------------------------------------------- inflow
+def _inflow_state(rho, u, p, dim, gamma=1.4):
+    vel = [u] + [0.0] * (dim - 1)
+    return [rho] + [rho * v for v in vel] + [p / (gamma - 1) + 0.5 * rho * sum(v * v for v in vel)]
+
+
+def test_inflow_ghosts_equal_a_padded_domain():
+    """An inflow side holds the given state in its three ghost layers: the residual
+    equals that of a domain extended by three cells of that state (transmissive
+    beyond them), restricted to the original cells."""
+    N = 40
+    U = I.random_state(1, (N,), seed=51, jumps=True)
+    qin = _inflow_state(1.3, 0.4, 1.1, 1)
+    cfg = O.Cfg(dim=1, n=(N,), bc=((O.INFLOW, O.TRANSMISSIVE),),
+                bc_state=[[qin, [0] * 3], [[0] * 3] * 2, [[0] * 3] * 2])
+    a = O.alpha(cfg, U)
+    R = O.residual_dirs(cfg, U, a)
+    pad = np.concatenate([np.array(qin)[:, None, None, None] * np.ones((3, 1, 1, 3)), U], axis=3)
+    cp = O.Cfg(dim=1, n=(N + 3,), hi=((N + 3) / N,), bc=((O.TRANSMISSIVE, O.TRANSMISSIVE),))
+    Rp = O.residual_dirs(cp, pad, a)
+    np.testing.assert_allclose(R, Rp[:, :, :, 3:], rtol=0, atol=1e-13 * np.abs(R).max())
+
+
+def test_inflow_of_the_interior_state_keeps_a_free_stream():
+    n = (16, 12)
+    qs = _inflow_state(1.2, 0.7, 0.9, 2)
+    st = [[qs, qs], [qs, qs], [[0] * 4] * 2]
+    cfg = O.Cfg(dim=2, n=n, bc=((O.INFLOW, O.INFLOW), (O.INFLOW, O.INFLOW)), bc_state=st)
+    U = np.ascontiguousarray(np.broadcast_to(np.array(qs)[:, None, None, None], cfg.shape))
+    R, _ = O.residual(cfg, U)
+    assert np.abs(R).max() < 1e-12
