@@ -56,8 +56,11 @@ typedef enum {
 /* Boundary rules (Sec. 4.5).  PERIODIC: ghosts copy the opposite interior
  * end.  TRANSMISSIVE: ghosts copy the nearest interior cell (zero-order
  * extrapolation; not defined in the paper).  REFLECTIVE: symmetry plane,
- * q(-2+l) = q(3-l) for l = 0,1,2 with the normal momentum negated. */
-typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_TRANSMISSIVE = 1, WENO_BC_REFLECTIVE = 2 } weno_bc;
+ * q(-2+l) = q(3-l) for l = 0,1,2 with the normal momentum negated.  INFLOW:
+ * all three ghost layers hold a given conserved state (weno_params.bc_state;
+ * the full-grid counterpart of the TT inflow rule, which zeroes the ghost rows
+ * and adds a rank-1 TT of the inflow state); not available for TT cores. */
+typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_TRANSMISSIVE = 1, WENO_BC_REFLECTIVE = 2, WENO_BC_INFLOW = 3 } weno_bc;
 
 /* WENO_FP64: every operation in FP64.  WENO_FP32_BULK: point fluxes, splitting
  * and reconstruction in FP32 on values taken relative to a reference state of
@@ -72,6 +75,16 @@ typedef enum { WENO_FP64 = 0, WENO_FP32_BULK = 1 } weno_precision;
  * Either way both are recomputed from every stage's state, and dt uses the
  * global max(|u| + a). */
 typedef enum { WENO_ALPHA_GLOBAL_NORM = 0, WENO_ALPHA_PER_DIR = 1 } weno_alpha_mode;
+
+/* Conservation law.  WENO_MODEL_EULER: the compressible Euler equations (nf =
+ * dim + 2 fields, Sec. 2.1).  WENO_MODEL_ADVECT: one scalar field under
+ * u_t + sum_d u_{x_d} = 0 (unit velocity in every direction, Sec. 5.1).
+ * WENO_MODEL_BURGERS: one scalar field under u_t + sum_d (u^2/2)_{x_d} = 0
+ * (Sec. 5.2).  The scalar laws split with alpha = max |f'(u)| (1, resp.
+ * max |u|) in every direction (weno_params.alpha_mode is ignored), run in
+ * WENO_FP64 only (WENO_FP32_BULK gives WENO_ERR_UNSUPPORTED), and treat a
+ * reflective side as a plain mirror (no component is negated). */
+typedef enum { WENO_MODEL_EULER = 0, WENO_MODEL_ADVECT = 1, WENO_MODEL_BURGERS = 2 } weno_model;
 
 typedef struct {
     int32_t dim;     /* 1, 2 or 3 */
@@ -88,6 +101,10 @@ typedef struct {
     int32_t bc[3][2];    /* weno_bc per direction, [low side, high side] */
     int32_t precision;   /* weno_precision */
     int32_t alpha_mode;  /* weno_alpha_mode */
+    double bc_state[3][2][5];  /* conserved state (rho, rho u, .., rho E; first nf
+                                * entries) of each WENO_BC_INFLOW side */
+    int32_t model;       /* weno_model */
+    int32_t reserved;
 } weno_params;
 
 /* Creates a handle for one grid and parameter set, allocates its scratch

@@ -56,6 +56,20 @@ __global__ void __launch_bounds__(256) k_alpha(const double *__restrict__ U, lon
     }
 }
 
+// Scalar laws: alpha = max |f'(u)| (1 for advection, |u| for Burgers).
+template <int M>
+__global__ void __launch_bounds__(256) k_alpha_scalar(const double *__restrict__ U, long long N, Ctl *ctl, int slot)
+{
+    double m = 0.0;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double u = __ldg(U + i);
+        bad |= !isfinite(u);
+        m = fmax(m, M == MODEL_ADVECT ? 1.0 : fabs(u));
+    }
+    block_max_publish(m, bad, &ctl->alpha[slot], &ctl->status);
+}
+
 __global__ void k_reset_slot(Ctl *ctl, int slot)
 {
     ctl->alpha[slot] = 0ull;
@@ -163,12 +177,15 @@ cudaError_t launch_sums(const double *U, int nf, long long N, double *partials, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
-                         int per_dir, cudaStream_t s)
+cudaError_t launch_alpha(int model, int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl,
+                         int slot, int per_dir, cudaStream_t s)
 {
     int blocks = (int)((N + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
+    if (model == MODEL_ADVECT) k_alpha_scalar<MODEL_ADVECT><<<blocks, 256, 0, s>>>(U, N, ctl, slot);
+    if (model == MODEL_BURGERS) k_alpha_scalar<MODEL_BURGERS><<<blocks, 256, 0, s>>>(U, N, ctl, slot);
+    if (model != MODEL_EULER) return cudaGetLastError();
 #define X(D, B) \
     if (dim == D && bulk == B) k_alpha<D, B><<<blocks, 256, 0, s>>>(U, N, gamma, ctl, slot, per_dir);
     X(1, false) X(2, false) X(3, false) X(1, true) X(2, true) X(3, true)

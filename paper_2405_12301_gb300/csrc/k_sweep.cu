@@ -19,6 +19,12 @@
 // in FP32 on differences from a per-line reference state (exact to FP32
 // relative precision of the differences), and only the final state update
 // U^(k+1) = U^(k) + D is an FP64 add.
+//
+// The model M selects the conservation law: the Euler equations (M = 0, the
+// only one with an FP32-bulk form), or one scalar field u under linear
+// advection with unit velocity in every direction (M = 1, f_d(u) = u, Sec. 5.1)
+// or Burgers' equation (M = 2, f_d(u) = u^2 / 2, Sec. 5.2).  The scalar laws
+// run through every direction of 1D, 2D and 3D grids with this kernel.
 #include <type_traits>
 
 #include "weno_dev.cuh"
@@ -33,9 +39,11 @@ template <> struct Tile<0> { static constexpr int W = 2, S = 122; };       // x:
 
 constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <int D, int DIR, bool BULK> struct Layout {
+template <int M> constexpr int nfields(int D) { return M == MODEL_EULER ? D + 2 : 1; }
+
+template <int M, int D, int DIR, bool BULK> struct Layout {
     using T = typename std::conditional<BULK, float, double>::type;
-    static constexpr int NF = D + 2, W = Tile<DIR>::W, S = Tile<DIR>::S, NP = S + 6, NI = S + 1;
+    static constexpr int NF = nfields<M>(D), W = Tile<DIR>::W, S = Tile<DIR>::S, NP = S + 6, NI = S + 1;
     static constexpr size_t fp_off = 0;
     static constexpr size_t fm_off = fp_off + sizeof(T) * NF * W * NP;
     static constexpr size_t F_off = fm_off + sizeof(T) * NF * W * NP;
@@ -43,10 +51,20 @@ template <int D, int DIR, bool BULK> struct Layout {
     static constexpr size_t bytes = ref_off + (BULK ? sizeof(RefState<D>) * W : 0);
 };
 
-template <int D, int DIR, bool BULK, int EPI>
+// Split fluxes f(+/-) = (f(u) +/- alpha u) / 2 of a scalar law (Eq. lax-friedrichs).
+template <int M>
+__device__ __forceinline__ void split_flux_scalar(double u, double alpha, double &fp, double &fm)
+{
+    const double f = M == MODEL_ADVECT ? u : 0.5 * u * u;
+    fp = 0.5 * (f + alpha * u);
+    fm = 0.5 * (f - alpha * u);
+}
+
+template <int M, int D, int DIR, bool BULK, int EPI>
 __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
 {
-    using L = Layout<D, DIR, BULK>;
+    static_assert(M == MODEL_EULER || !BULK, "the FP32-bulk form exists for the Euler equations only");
+    using L = Layout<M, D, DIR, BULK>;
     using T = typename L::T;
     constexpr int NF = L::NF, W = L::W, S = L::S, NP = L::NP, NI = L::NI;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -86,7 +104,7 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     const T eps = BULK ? (T)a.eps_f : (T)a.eps;
 
     // ---- phase 0 (FP32-bulk): reference state of every line
-    if (BULK) {
+    if constexpr (BULK) {
         for (int w = threadIdx.x; w < W; w += NT) {
             long long base;
             const bool ok = line(w, base);
@@ -111,13 +129,16 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
             int c = c0 - 3 + p;
             c = c < n + 2 ? c : n + 2;
             bool flip;
-            const int cm = ghost_source(c, n, a.bc[DIR][0], a.bc[DIR][1], flip);
+            int inflow;
+            const int cm = ghost_map(c, n, a.bc[DIR][0], a.bc[DIR][1], flip, inflow);
             const double *src = a.U + base + (long long)cm * st;
             double q[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(src + f * N);
-            if (flip) q[1 + DIR] = -q[1 + DIR];
-            if constexpr (BULK) {
+            for (int f = 0; f < NF; ++f) q[f] = inflow >= 0 ? a.bc_state[DIR][inflow][f] : __ldg(src + f * N);
+            if (M == MODEL_EULER && flip) q[1 + DIR] = -q[1 + DIR];
+            if constexpr (M != MODEL_EULER) {
+                split_flux_scalar<M>(q[0], alpha, fpv[0], fmv[0]);
+            } else if constexpr (BULK) {
                 float dq[NF];
                 diff_from_ref<D>(q, sref[w], dq);
                 split_flux_diff<D, DIR>(dq, sref[w], alpha_f, a.gm1_f, fpv, fmv);
@@ -218,7 +239,10 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
                     a.Uout[f * N + cell] = out[f];
                 }
                 bool b;
-                if constexpr (BULK) {
+                if constexpr (M != MODEL_EULER) {  // |f'(u)|: 1 for advection, |u| for Burgers
+                    b = !isfinite(out[0]);
+                    cmax = fmax(cmax, M == MODEL_ADVECT ? 1.0 : fabs(out[0]));
+                } else if constexpr (BULK) {
                     float qf[NF];
 #pragma unroll
                     for (int f = 0; f < NF; ++f) qf[f] = f64_to_f32(out[f]);
@@ -234,52 +258,60 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
         if (BULK) cmax = (double)cmaxf;
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
         // 1D: |u_x| + a equals |u| + a, so the x slot takes the same maximum
-        if (a.per_dir) block_max_publish(cmax, false, &a.ctl->alpha_dir[a.slot_out][0], &a.ctl->status);
+        if (M == MODEL_EULER && D == 1 && a.per_dir) block_max_publish(cmax, false, &a.ctl->alpha_dir[a.slot_out][0], &a.ctl->status);
     }
 }
 
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-template <int D, int DIR, bool BULK, int EPI>
+template <int M, int D, int DIR, bool BULK, int EPI>
 static cudaError_t launch_t(const SweepArgs &a, cudaStream_t s)
 {
-    using L = Layout<D, DIR, BULK>;
+    using L = Layout<M, D, DIR, BULK>;
     dim3 grid;
     if (DIR == 0) grid = dim3(cdiv(a.n[0], L::S), cdiv(a.n[1], L::W), (unsigned)a.n[2]);
     else if (DIR == 1) grid = dim3(cdiv(a.n[0], L::W), cdiv(a.n[1], L::S), (unsigned)a.n[2]);
     else grid = dim3(cdiv(a.n[0], L::W), (unsigned)a.n[1], cdiv(a.n[2], L::S));
-    k_sweep<D, DIR, BULK, EPI><<<grid, NT, L::bytes, s>>>(a);
+    k_sweep<M, D, DIR, BULK, EPI><<<grid, NT, L::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int D, int DIR, bool BULK, int EPI>
+template <int M, int D, int DIR, bool BULK, int EPI>
 static cudaError_t attr_t()
 {
-    using L = Layout<D, DIR, BULK>;
-    return cudaFuncSetAttribute(k_sweep<D, DIR, BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using L = Layout<M, D, DIR, BULK>;
+    return cudaFuncSetAttribute(k_sweep<M, D, DIR, BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)L::bytes);
 }
 
-// 1D grids (2D and 3D grids run in the fused k_xy and k_z kernels).
-#define WG_SWEEP_TABLE(X, B) X(1, 0, B, EPI_RHS) X(1, 0, B, EPI_STAGE)
+// Euler: 1D grids only (2D and 3D grids run in the fused k_xy and k_z kernels).
+// Scalar laws (FP64): every direction; the first stores, the middle one of 3D
+// adds, the last runs the residual or stage epilogue.
+#define WG_SWEEP_TABLE(X)                                                                       \
+    X(MODEL_EULER, 1, 0, false, EPI_RHS) X(MODEL_EULER, 1, 0, false, EPI_STAGE)                  \
+    X(MODEL_EULER, 1, 0, true, EPI_RHS) X(MODEL_EULER, 1, 0, true, EPI_STAGE)                    \
+    WG_SCALAR_ROWS(X, MODEL_ADVECT) WG_SCALAR_ROWS(X, MODEL_BURGERS)
+#define WG_SCALAR_ROWS(X, M)                                                                     \
+    X(M, 1, 0, false, EPI_RHS) X(M, 1, 0, false, EPI_STAGE)                                      \
+    X(M, 2, 0, false, EPI_STORE) X(M, 2, 1, false, EPI_RHS) X(M, 2, 1, false, EPI_STAGE)         \
+    X(M, 3, 0, false, EPI_STORE) X(M, 3, 1, false, EPI_ADD) X(M, 3, 2, false, EPI_RHS)           \
+    X(M, 3, 2, false, EPI_STAGE)
 
 cudaError_t sweep_set_attributes()
 {
     cudaError_t e = cudaSuccess, r;
-#define X(D, DIR, B, E) \
-    if ((r = attr_t<D, DIR, B, E>()) != cudaSuccess) e = r;
-    WG_SWEEP_TABLE(X, false)
-    WG_SWEEP_TABLE(X, true)
+#define X(M, D, DIR, B, E) \
+    if ((r = attr_t<M, D, DIR, B, E>()) != cudaSuccess) e = r;
+    WG_SWEEP_TABLE(X)
 #undef X
     return e;
 }
 
-cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
+cudaError_t launch_sweep(int model, int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
 {
-#define X(D, DIR, B, E) \
-    if (dim == D && dir == DIR && bulk == B && epi == E) return launch_t<D, DIR, B, E>(a, s);
-    WG_SWEEP_TABLE(X, false)
-    WG_SWEEP_TABLE(X, true)
+#define X(M, D, DIR, B, E) \
+    if (model == M && dim == D && dir == DIR && bulk == B && epi == E) return launch_t<M, D, DIR, B, E>(a, s);
+    WG_SWEEP_TABLE(X)
 #undef X
     return cudaErrorInvalidValue;
 }

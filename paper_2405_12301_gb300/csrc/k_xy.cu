@@ -48,7 +48,7 @@ template <int D, bool BULK> struct Layout {
 };
 }  // namespace xy
 
-template <int D, bool BULK, int EPI>
+template <int D, bool BULK, int EPI, bool PD>
 __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
 {
     using namespace xy;
@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     const double dt = __longlong_as_double(dtbits);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     // LF constants of the x and y splittings: the global alpha, or per direction
-    const double alx = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha;
-    const double aly = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha;
+    const double alx = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha;
+    const double aly = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha;
 
     const int nx = a.n[0], ny = a.n[1];
     const long long N = a.N;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
         __syncthreads();
     }
     const T alX = BULK ? (T)f64_to_f32(alx) : (T)alx;
-    const T alY = BULK ? (T)f64_to_f32(aly) : (T)aly;
+    const T alY = !PD ? alX : (BULK ? (T)f64_to_f32(aly) : (T)aly);
     const double gm1 = a.gamma - 1.0;
     // interior tiles (halo inside the grid) skip the boundary rule
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
@@ -111,10 +111,17 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
         int cx = x0 + lx, cy = y0 + ly;
         bool fx_ = false, fy_ = false;
         if (!interior) {
+            int inx, iny;
             cx = cx < nx + 2 ? cx : nx + 2;
             cy = cy < ny + 2 ? cy : ny + 2;
-            cx = ghost_source(cx, nx, a.bc[0][0], a.bc[0][1], fx_);
-            cy = ghost_source(cy, ny, a.bc[1][0], a.bc[1][1], fy_);
+            cx = ghost_map(cx, nx, a.bc[0][0], a.bc[0][1], fx_, inx);
+            cy = ghost_map(cy, ny, a.bc[1][0], a.bc[1][1], fy_, iny);
+            if (inx >= 0 || iny >= 0) {  // a ghost of an inflow side holds the given state
+                const double *st = inx >= 0 ? a.bc_state[0][inx] : a.bc_state[1][iny];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) q[f] = st[f];
+                return;
+            }
         }
         const double *src = a.U + zoff + (long long)cy * nx + cx;
 #pragma unroll
@@ -282,10 +289,10 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<D>(qn, a.gamma_f, bad);
-            if (a.per_dir && !bad) dirspeeds_f32<D>(qn, a.gamma_f, sd);
+            if (PD && !bad) dirspeeds_f32<D>(qn, a.gamma_f, sd);
         }
         block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-        if (a.per_dir) {
+        if constexpr (PD) {
 #pragma unroll
             for (int e = 0; e < D; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
         }
@@ -305,37 +312,39 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                 a.Uout[f * N + cell] = out[f];
             }
             cmax = wavespeed_f64<D>(out, a.gamma, bad);
-            if (a.per_dir && !bad) dirspeeds_f64<D>(out, a.gamma, sd);
+            if (PD && !bad) dirspeeds_f64<D>(out, a.gamma, sd);
         }
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-        if (a.per_dir) {
+        if constexpr (PD) {
 #pragma unroll
             for (int e = 0; e < D; ++e) block_max_publish(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
         }
     }
 }
 
-template <int D, bool BULK, int EPI>
+template <int D, bool BULK, int EPI, bool PD>
 static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
 {
     using L = xy::Layout<D, BULK>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_xy<D, BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_xy<D, BULK, EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)L::bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[0] + xy::TX - 1) / xy::TX), (unsigned)((a.n[1] + xy::TY - 1) / xy::TY),
               (unsigned)a.n[2]);
-    k_xy<D, BULK, EPI><<<grid, xy::NT, L::bytes, s>>>(a);
+    k_xy<D, BULK, EPI, PD><<<grid, xy::NT, L::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
 {
-#define X(D, B, E) \
-    if (dim == D && bulk == B && epi == E) return launch_xy_t<D, B, E>(a, s);
+#define X(D, B, E)                                            \
+    if (dim == D && bulk == B && epi == E)                    \
+        return a.per_dir ? launch_xy_t<D, B, E, true>(a, s)   \
+                         : launch_xy_t<D, B, E, false>(a, s);
     X(2, false, EPI_RHS) X(2, false, EPI_STAGE) X(3, false, EPI_STORE)
     X(2, true, EPI_RHS) X(2, true, EPI_STAGE) X(3, true, EPI_STORE)
 #undef X

@@ -31,7 +31,7 @@ template <bool BULK> struct Layout {
 };
 }  // namespace zs
 
-template <bool BULK, int EPI>
+template <bool BULK, int EPI, bool PD>
 __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
 {
     using namespace zs;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
-    const double alpha = a.per_dir ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][2])
+    const double alpha = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][2])
                                    : __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
 
     const int nx = a.n[0], nz = a.n[2];
@@ -85,9 +85,15 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         int cx = x0 + lx, cz = z0 + lz;
         bool fz_ = false;
         if (!interior) {
+            int inz;
             cx = cx < nx ? cx : nx - 1;  // columns beyond the grid only feed cells that are not written
             cz = cz < nz + 2 ? cz : nz + 2;
-            cz = ghost_source(cz, nz, a.bc[2][0], a.bc[2][1], fz_);
+            cz = ghost_map(cz, nz, a.bc[2][0], a.bc[2][1], fz_, inz);
+            if (inz >= 0) {  // a ghost of an inflow side holds the given state
+#pragma unroll
+                for (int f = 0; f < NF; ++f) q[f] = a.bc_state[2][inz][f];
+                return;
+            }
         }
         const double *src = a.U + yoff + (long long)cz * sz + cx;
 #pragma unroll
@@ -194,10 +200,10 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
-            if (a.per_dir && !bad) dirspeeds_f32<3>(qn, a.gamma_f, sd);
+            if (PD && !bad) dirspeeds_f32<3>(qn, a.gamma_f, sd);
         }
         block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-        if (a.per_dir) {
+        if constexpr (PD) {
 #pragma unroll
             for (int e = 0; e < 3; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
         }
@@ -215,36 +221,40 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
                 a.Uout[f * N + cell] = out[f];
             }
             cmax = wavespeed_f64<3>(out, a.gamma, bad);
-            if (a.per_dir && !bad) dirspeeds_f64<3>(out, a.gamma, sd);
+            if (PD && !bad) dirspeeds_f64<3>(out, a.gamma, sd);
         }
         block_max_publish(cmax, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-        if (a.per_dir) {
+        if constexpr (PD) {
 #pragma unroll
             for (int e = 0; e < 3; ++e) block_max_publish(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
         }
     }
 }
 
-template <bool BULK, int EPI>
+template <bool BULK, int EPI, bool PD>
 static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
 {
     using L = zs::Layout<BULK>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)L::bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ), (unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1]);
-    k_z<BULK, EPI><<<grid, zs::NT, L::bytes, s>>>(a);
+    k_z<BULK, EPI, PD><<<grid, zs::NT, L::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
 {
-    if (bulk) return epi == EPI_STAGE ? launch_z_t<true, EPI_STAGE>(a, s) : launch_z_t<true, EPI_RHS>(a, s);
-    return epi == EPI_STAGE ? launch_z_t<false, EPI_STAGE>(a, s) : launch_z_t<false, EPI_RHS>(a, s);
+#define X(B, E, P) \
+    if (bulk == B && epi == E && (a.per_dir != 0) == P) return launch_z_t<B, E, P>(a, s);
+    X(false, EPI_RHS, false) X(false, EPI_STAGE, false) X(true, EPI_RHS, false) X(true, EPI_STAGE, false)
+    X(false, EPI_RHS, true) X(false, EPI_STAGE, true) X(true, EPI_RHS, true) X(true, EPI_STAGE, true)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace wg

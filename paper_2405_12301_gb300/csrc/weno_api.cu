@@ -159,7 +159,11 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
         return fail(nullptr, WENO_ERR_ARG, "weno_init: bad alpha_mode");
     for (int d = 0; d < 3; ++d)
         for (int s = 0; s < 2; ++s)
-            if (p.bc[d][s] < 0 || p.bc[d][s] > 2) return fail(nullptr, WENO_ERR_ARG, "weno_init: bad boundary rule");
+            if (p.bc[d][s] < 0 || p.bc[d][s] > 3) return fail(nullptr, WENO_ERR_ARG, "weno_init: bad boundary rule");
+    if (p.model < WENO_MODEL_EULER || p.model > WENO_MODEL_BURGERS)
+        return fail(nullptr, WENO_ERR_ARG, "weno_init: bad model");
+    if (p.model != WENO_MODEL_EULER && p.precision != WENO_FP64)
+        return fail(nullptr, WENO_ERR_UNSUPPORTED, "weno_init: the scalar models run in FP64 only");
     weno_ctx *h = new weno_ctx();
     h->p = p;
     h->stream = (cudaStream_t)cuda_stream;
@@ -169,7 +173,7 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
             return fail(nullptr, WENO_ERR_ARG, "weno_init: dim must be 1, 2 or 3");
         }
         h->dim = grid->dim;
-        h->nf = grid->dim + 2;
+        h->nf = p.model == WENO_MODEL_EULER ? grid->dim + 2 : 1;
         h->N = 1;
         for (int d = 0; d < 3; ++d) {
             const long long nd = d < grid->dim ? grid->n[d] : 1;
@@ -189,6 +193,10 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
         if ((h->dim == 2 && h->n[1] > 65535ll * 8) || (h->dim == 3 && (h->n[1] > 65535 || h->n[2] > 65535))) {
             delete h;
             return fail(nullptr, WENO_ERR_ARG, "weno_init: need ny <= 524280 (2D), ny, nz <= 65535 (3D)");
+        }
+        if (p.model != WENO_MODEL_EULER && h->dim == 2 && h->n[1] > 65535ll * 2) {
+            delete h;
+            return fail(nullptr, WENO_ERR_ARG, "weno_init: scalar models need ny <= 131070 (2D)");
         }
     }
     static bool attrs = false;
@@ -269,6 +277,8 @@ static SweepArgs base_args(weno_ctx *h)
         a.inv_h[d] = 1.0 / h->h[d];
         a.bc[d][0] = h->p.bc[d][0];
         a.bc[d][1] = h->p.bc[d][1];
+        for (int sd = 0; sd < 2; ++sd)
+            for (int f = 0; f < 5; ++f) a.bc_state[d][sd][f] = h->p.bc_state[d][sd][f];
     }
     a.stride[0] = 1;
     a.stride[1] = h->n[0];
@@ -280,7 +290,8 @@ static SweepArgs base_args(weno_ctx *h)
     a.eps_f = (float)h->p.eps_weno;
     for (int d = 0; d < 3; ++d) a.inv_h_f[d] = (float)a.inv_h[d];
     a.acc = h->acc;
-    a.per_dir = h->p.alpha_mode == WENO_ALPHA_PER_DIR ? 1 : 0;
+    // a scalar law has one wavespeed |f'(u)| for every direction
+    a.per_dir = h->p.alpha_mode == WENO_ALPHA_PER_DIR && h->p.model == WENO_MODEL_EULER ? 1 : 0;
     return a;
 }
 
@@ -291,8 +302,13 @@ static bool bulk(const weno_ctx *h) { return h->p.precision == WENO_FP32_BULK; }
 //   per z-plane (stores), then the z kernel (adds, and runs `last`).
 static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
 {
-    if (h->dim == 1) {
-        CK(h, launch(h, 3, s, [&] { return launch_sweep(1, 0, bulk(h), last, a, s); }));
+    if (h->p.model != WENO_MODEL_EULER) {  // scalar laws: one sweep per direction
+        for (int d = 0; d < h->dim; ++d) {
+            const int epi = d == h->dim - 1 ? last : (d == 0 ? EPI_STORE : EPI_ADD);
+            CK(h, launch(h, 3, s, [&] { return launch_sweep(h->p.model, h->dim, d, false, epi, a, s); }));
+        }
+    } else if (h->dim == 1) {
+        CK(h, launch(h, 3, s, [&] { return launch_sweep(MODEL_EULER, 1, 0, bulk(h), last, a, s); }));
     } else if (h->dim == 2) {
         CK(h, launch(h, 4, s, [&] { return launch_xy(2, bulk(h), last, a, s); }));
     } else {
@@ -329,8 +345,8 @@ static int enqueue_alpha0(weno_ctx *h, const double *U, cudaStream_t s)
 {
     CK(h, launch(h, 7, s, [&] { return launch_reset_slot(h->ctl, 0, s); }));
     CK(h, launch(h, 6, s, [&] {
-           return launch_alpha(h->dim, bulk(h), U, h->N, h->p.gamma, h->ctl, 0,
-                               h->p.alpha_mode == WENO_ALPHA_PER_DIR ? 1 : 0, s);
+           return launch_alpha(h->p.model, h->dim, bulk(h), U, h->N, h->p.gamma, h->ctl, 0,
+                               h->p.alpha_mode == WENO_ALPHA_PER_DIR && h->p.model == WENO_MODEL_EULER ? 1 : 0, s);
        }));
     return WENO_OK;
 }
@@ -534,6 +550,8 @@ extern "C" int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int3
             c.n[m] = I.n[m];
             c.h[m] = I.h[m];
             for (int sd = 0; sd < 2; ++sd) {
+                if (I.bc[m][sd] == WENO_BC_INFLOW)
+                    return fail(h, WENO_ERR_UNSUPPORTED, "weno_cross_eval: inflow boundaries are not implemented for TT cores");
                 if (I.bc[m][sd] < 0 || I.bc[m][sd] > 2) return fail(h, WENO_ERR_ARG, "weno_cross_eval: bad boundary rule");
                 c.bc[m][sd] = I.bc[m][sd];
             }

@@ -13,7 +13,7 @@
 
 namespace wg {
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 enum { ST_NONPHYSICAL = 1, ST_TIMEOUT = 2, ST_BADINDEX = 4 };
 
 // Device control block of one handle: time, step size and the stage alphas.
@@ -109,6 +109,25 @@ __device__ __forceinline__ int ghost_source(int c, int n, int bclo, int bchi, bo
         return 2 * n - 1 - c;
     }
     return c;
+}
+
+// Full-grid ghost mapping: as ghost_source, plus inflow sides, whose ghosts
+// hold a given state: *inflow is set to the side (0 low, 1 high) and a valid
+// interior index is returned (the caller replaces the value); -1 otherwise.
+__device__ __forceinline__ int ghost_map(int c, int n, int bclo, int bchi, bool &flip, int &inflow)
+{
+    inflow = -1;
+    if (c < 0 && bclo == BC_INFLOW) {
+        flip = false;
+        inflow = 0;
+        return 0;
+    }
+    if (c >= n && bchi == BC_INFLOW) {
+        flip = false;
+        inflow = 1;
+        return n - 1;
+    }
+    return ghost_source(c, n, bclo, bchi, flip);
 }
 
 // ---------------------------------------------------------------- WENO5-JS

@@ -9,6 +9,8 @@ struct Ctl;
 
 // Epilogue of a sweep kernel (what it does with the direction's residual).
 enum Epi { EPI_STORE = 0, EPI_ADD = 1, EPI_RHS = 2, EPI_STAGE = 3 };
+// Conservation law: Euler (nf = dim + 2), scalar advection or Burgers (nf = 1).
+enum Model { MODEL_EULER = 0, MODEL_ADVECT = 1, MODEL_BURGERS = 2 };
 
 struct SweepArgs {
     const double *U;     // stencil state U^(k) (device, FP64 SoA)
@@ -21,6 +23,7 @@ struct SweepArgs {
     int n[3];
     long long stride[3]; // 1, nx, nx * ny
     int bc[3][2];
+    double bc_state[3][2][5];  // conserved state held by the ghosts of an inflow side
     double inv_h[3];
     double gamma;
     double eps;
@@ -34,14 +37,14 @@ struct SweepArgs {
 };
 
 // Launches the sweep of direction dir for a dim-dimensional grid.
-cudaError_t launch_sweep(int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_sweep(int model, int dim, int dir, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 cudaError_t sweep_set_attributes();
 // Fused x+y residual of a 2D grid (EPI_RHS / EPI_STAGE) or of the z-planes of a 3D grid (EPI_STORE).
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 // z direction of a 3D grid, adding the accumulator and ending the residual (EPI_RHS / EPI_STAGE).
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 
-cudaError_t launch_alpha(int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
+cudaError_t launch_alpha(int model, int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
                          int per_dir, cudaStream_t s);
 cudaError_t launch_reset_slot(Ctl *ctl, int slot, cudaStream_t s);
 cudaError_t launch_step_begin(Ctl *ctl, cudaStream_t s);

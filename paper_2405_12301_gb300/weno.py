@@ -13,9 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libweno_gb300.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 FP64, FP32_BULK = 0, 1
 ALPHA_GLOBAL_NORM, ALPHA_PER_DIR = 0, 1
+MODEL_EULER, MODEL_ADVECT, MODEL_BURGERS = 0, 1, 2
 CROSS_FP64_CHECK = 1
 
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
@@ -38,7 +39,8 @@ class weno_grid(C.Structure):
 
 class weno_params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("eps_weno", C.c_double), ("cfl", C.c_double),
-                ("bc", (C.c_int32 * 2) * 3), ("precision", C.c_int32), ("alpha_mode", C.c_int32)]
+                ("bc", (C.c_int32 * 2) * 3), ("precision", C.c_int32), ("alpha_mode", C.c_int32),
+                ("bc_state", ((C.c_double * 5) * 2) * 3), ("model", C.c_int32), ("reserved", C.c_int32)]
 
 
 class weno_tt_instance(C.Structure):
@@ -112,7 +114,8 @@ def _stream():
 
 # ------------------------------------------------------------ thin wrappers
 def weno_init(dim=None, n=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=1.4, eps_weno=1e-6, cfl=0.5,
-              bc=((BC_PERIODIC, BC_PERIODIC),) * 3, precision=FP64, alpha_mode=ALPHA_GLOBAL_NORM, stream=None):
+              bc=((BC_PERIODIC, BC_PERIODIC),) * 3, precision=FP64, alpha_mode=ALPHA_GLOBAL_NORM, stream=None,
+              bc_state=None, model=MODEL_EULER):
     """Returns a handle (c_void_p).  dim=None makes a cross-eval-only handle."""
     g = None
     if dim is not None:
@@ -127,7 +130,12 @@ def weno_init(dim=None, n=None, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), gamma=1.
     p.gamma, p.eps_weno, p.cfl = gamma, eps_weno, cfl
     for k in range(3):
         p.bc[k][0], p.bc[k][1] = bc[k] if k < len(bc) else (BC_PERIODIC, BC_PERIODIC)
-    p.precision, p.alpha_mode = precision, alpha_mode
+    p.precision, p.alpha_mode, p.model = precision, alpha_mode, model
+    if bc_state is not None:  # [3][2][nf] conserved states of the inflow sides
+        for k in range(3):
+            for side in range(2):
+                for f, v in enumerate(bc_state[k][side]):
+                    p.bc_state[k][side][f] = float(v)
     h = C.c_void_p()
     code = lib().weno_init(C.byref(h), C.byref(g) if g is not None else None, C.byref(p),
                            stream if stream is not None else _stream())
@@ -255,7 +263,8 @@ class Solver:
     def __init__(self, dim, n, lo=None, hi=None, **kw):
         lo = lo if lo is not None else (0.0,) * dim
         hi = hi if hi is not None else (1.0,) * dim
-        self.dim, self.n, self.nf = dim, tuple(n), dim + 2
+        self.dim, self.n = dim, tuple(n)
+        self.nf = dim + 2 if kw.get("model", MODEL_EULER) == MODEL_EULER else 1
         self.h = weno_init(dim, n, lo, hi, **kw)
 
     def close(self):

@@ -46,3 +46,8 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     p.alpha_mode = weno.ALPHA_GLOBAL_NORM
     p.bc[0][1] = 9    # not a weno_bc
     assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_ARG
+    p.bc[0][1] = weno.BC_INFLOW
+    p.model = 5       # not a weno_model
+    assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_ARG
+    p.model, p.precision = weno.MODEL_BURGERS, weno.FP32_BULK  # scalar laws are FP64 only
+    assert L.weno_init(ctypes.byref(h), None, ctypes.byref(p), None) == weno.ERR_UNSUPPORTED

@@ -149,6 +149,20 @@ def test_cross_eval_bad_index_is_reported(W):
     W.weno_destroy(h)
 
 
+def test_cross_eval_rejects_inflow_sides(W):
+    """Inflow ghosts are a full-grid rule only: the TT path refuses them before
+    launching anything."""
+    inst = make_instance(6, [8, 9, 10], [2, 3], (O.PERIODIC,) * 2)
+    inst["bc"] = ((O.INFLOW, O.TRANSMISSIVE),) + ((O.PERIODIC, O.PERIODIC),) * 2
+    h = W.weno_init(None)
+    sets, _ = make_sets(inst, 0, 6, True, which={(0, 0)})
+    with pytest.raises(W.WenoError) as e:
+        W.weno_cross_eval(h, [dev_instance(inst)], sets, fp64_check=True)
+    assert e.value.code == W.ERR_UNSUPPORTED
+    W.weno_sync(h)
+    W.weno_destroy(h)
+
+
 def test_cross_eval_full_workload_sampled(W):
     """The benchmark's 64-instance workload (n in {64..512}, ranks 2..32), all 9 sets
     per instance in one launch; a few fibers per set are checked against the oracle."""

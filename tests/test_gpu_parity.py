@@ -49,7 +49,8 @@ def host(t):
 
 def solver(W, cfg, precision=0, cfl=0.5):
     return W.Solver(cfg.dim, cfg.n[:cfg.dim], cfg.lo[:cfg.dim], cfg.hi[:cfg.dim], gamma=cfg.gamma,
-                    eps_weno=cfg.eps, cfl=cfl, bc=cfg.bc, precision=precision, alpha_mode=cfg.alpha_mode)
+                    eps_weno=cfg.eps, cfl=cfl, bc=cfg.bc, precision=precision, alpha_mode=cfg.alpha_mode,
+                    bc_state=cfg.bc_state)
 
 
 def fp64_rhs_tol(cfg, U, Rref, alpha):
@@ -233,19 +234,24 @@ def test_nonphysical_state_is_reported_not_faulted(W):
 
 
 # ------------------------------------------------------------- FP32-bulk path
-def _variation_tol(cfg, U, Rref, alpha):
+def _variation_tol(cfg, U, Rref, alpha, ghosts=()):
     """32 * 2^-24 * V_f / h + 1e-6 |R_f|_inf with V_f = (1 + alpha) * max line variation of
-    (U_f, rho E), an upper bound of the variation of the split fluxes along a line."""
+    (U_f, rho E), an upper bound of the variation of the split fluxes along a line.
+    ghosts: further states a line can hold (inflow ghost states)."""
     nf = U.shape[0]
     hmin = min(cfg.spacing(d) for d in range(cfg.dim))
+    G = np.asarray(ghosts, dtype=np.float64).reshape(-1, nf)
     tol = np.empty_like(Rref)
     for f in range(nf):
         v = 0.0
         for d in range(cfg.dim):
             ax = 3 - d
             for g in (f, nf - 1, 0):
-                v = max(v, float((U[g].max(axis=ax - 1) - U[g].min(axis=ax - 1)).max()))
-        V = (1.0 + alpha) * v * (1.0 + np.abs(U[1:nf - 1]).max() / np.abs(U[0]).min())
+                hi_ = np.maximum(U[g].max(axis=ax - 1), G[:, g].max(initial=-np.inf))
+                lo_ = np.minimum(U[g].min(axis=ax - 1), G[:, g].min(initial=np.inf))
+                v = max(v, float((hi_ - lo_).max()))
+        mom = max(np.abs(U[1:nf - 1]).max(), np.abs(G[:, 1:nf - 1]).max(initial=0.0))
+        V = (1.0 + alpha) * v * (1.0 + mom / min(np.abs(U[0]).min(), np.abs(G[:, 0]).min(initial=np.inf)))
         tol[f] = 32 * 2.0 ** -24 * V / hmin + 1e-6 * np.abs(Rref[f]).max()
     return tol
 
@@ -425,3 +431,42 @@ def test_per_direction_alpha_bulk_matches_oracle(W):
     # per-direction splitting must differ from the global one on this state
     Rg, _ = O.residual(O.Cfg(dim=2, n=(64, 48)), U)
     assert np.abs(Rg - Rref).max() > 1e3 * np.abs(host(Rd) - Rref).max()
+
+
+# --------------------------------------------------------------- inflow sides
+def _qin(dim, rho, u, p):
+    vel = [u] + [0.3 * u] * (dim - 1)
+    return [rho] + [rho * v for v in vel] + [p / 0.4 + 0.5 * rho * sum(v * v for v in vel)]
+
+
+IN = O.INFLOW
+INFLOW_CASES = [
+    (1, (150,), ((IN, T),)),
+    (2, (70, 45), ((IN, T), (R, IN))),
+    (3, (36, 30, 27), ((IN, P), (T, T), (R, IN))),
+]
+
+
+@pytest.mark.parametrize("dim,n,bc", INFLOW_CASES)
+def test_inflow_fp64_matches_oracle(W, dim, n, bc):
+    nf = dim + 2
+    st = [[_qin(dim, 1.4, 0.9, 1.2), _qin(dim, 0.8, -0.3, 0.7)],
+          [_qin(dim, 1.1, 0.2, 1.0), _qin(dim, 0.9, -0.5, 0.8)],
+          [_qin(dim, 1.2, 0.4, 0.9), _qin(dim, 1.0, -0.2, 1.1)]]
+    st = [[side[:nf] + [0.0] * (5 - nf) for side in d] for d in st]
+    cfg = O.Cfg(dim=dim, n=n, bc=bc, bc_state=st)
+    U = I.random_state(dim, n, seed=500 + sum(n), jumps=True)
+    Rref, aref = O.residual(cfg, U)
+    s = solver(W, cfg)
+    Rd = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    s.rhs(dev(U), Rd)
+    assert (np.abs(host(Rd) - Rref) <= fp64_rhs_tol(cfg, U, Rref, aref[0])).all()
+    Uref, steps, t = O.run(cfg, U, 0.03, cfl=0.5)
+    Ud = dev(U)
+    s.set_time(0.0)
+    assert s.run(Ud, 0.03, graph_steps=4) == steps
+    assert rel_field_err(host(Ud), Uref) <= 1e-10
+    sb = solver(W, cfg, precision=1)
+    sb.rhs(dev(U), Rd)
+    used = [st[k][side][:nf] for k in range(dim) for side in range(2) if bc[k][side] == IN]
+    assert (np.abs(host(Rd) - Rref) <= _variation_tol(cfg, U, Rref, aref[0], used)).all()
