@@ -289,7 +289,7 @@ def job_value(units_per_rank, world, seconds):
     return units_per_rank * world / seconds / 1e6
 
 
-KIND_NAMES = ["unused0", "unused1", "xy_plane_3d", "sweep_x_1d", "xy_fused_2d", "sweep_z_3d", "alpha", "small"]
+KIND_NAMES = ["unused0", "unused1", "xy_plane_3d", "sweep", "xy_fused_2d", "sweep_z_3d", "alpha", "small"]
 
 
 def kernel_table(kms, kn):
@@ -361,6 +361,50 @@ def bench_cross(weno, I, torch, reps=10):
                          "ms_per_launch": kernel_ms}}
 
 
+def flops_scalar_sweep(model, last):
+    """Algorithmic flops per cell of one direction of a scalar law: split fluxes
+    (advection: alpha u, two adds, two halvings = 5; Burgers adds u^2/2 = 7),
+    interface flux 137, flux difference 3; the last direction adds the
+    accumulator (1), the stage combination (4) and |f'(u)| (Burgers: 1)."""
+    f = 137 + (5 if model == 1 else 7) + 3
+    if last:
+        f += 1 + 4 + (0 if model == 1 else 1)
+    return f
+
+
+def bench_scalar(weno, I, torch, steps=4, warmup=3, N=256):
+    """Scalar linear advection with unit velocity (Sec. 5.1 set-up, u0 = sin(2 pi
+    (x + y + z)) on [0,1)^3, periodic) on 256^3 in FP64 with the CFL dt: three
+    per-direction sweep launches per stage.  Inputs: 4 FP64 arrays of 134 MB."""
+    n = (N, N, N)
+    cells = N ** 3
+    s = weno.Solver(3, n, model=weno.MODEL_ADVECT, precision=weno.FP64)
+    U = torch.from_numpy(I.scalar_sine(3, n)).cuda()
+    s.set_time(0.0)
+    s.run(U, 1e30, max_steps=warmup, graph_steps=0)
+    s.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    taken = s.run(U, 1e30, max_steps=steps, graph_steps=0)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kms, kn, launches = s.profile_read()
+    s.close()
+    assert taken == steps
+    fl = sum(flops_scalar_sweep(1, d == 2) for d in range(3))
+    sweep_ms = kms[3]
+    achieved = cells * fl * 3 * steps / (sweep_ms * 1e-3) / 1e12
+    return {"workload": "scalar_advection_3d_256cube", "value": cells * 3 * steps / (ms * 1e-3) / 1e6,
+            "unit": "Mcell-stage/s", "dtype": "f64", "steps": steps, "ms_per_step": ms / steps,
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None, "kernel": "sweep",
+                         "ms_per_launch": sweep_ms / max(1, kn[3]), "flops_per_cell_stage": fl,
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,7 +413,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-cross", action="store_true")
+    ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -429,6 +473,7 @@ def main():
 
     cross = bench_cross(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     acc = accuracy(weno, I, torch) if rank == 0 else None
+    scalar = bench_scalar(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     rl = roofline(w, True, kms, kn, cells)
     rl64 = roofline(w, False, kms64, kn64, cells)
     step_tflops = value * 1e6 * flops_cell_stage(w["dim"]) / 1e12 / world
@@ -450,6 +495,7 @@ def main():
                  "kernels_ms_per_launch": kernel_table(kms64, kn64)},
         "accuracy": acc,
         "cross_eval": cross,
+        "scalar_advection": scalar,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
