@@ -175,8 +175,9 @@ int weno_sync(weno_handle h);
  *   kind 2: fused x+y kernel of a 3D grid (stores to the accumulator),
  *   kind 3: 1D sweep, kind 4: fused x+y kernel of a 2D grid, kind 5: z sweep
  *           of a 3D grid (3..5 end a residual: stage combination or L(U)),
- *   kind 6: wavespeed max, kind 7: step control and other small kernels
- *   (kinds 0 and 1 are unused).
+ *   kind 6: wavespeed max, kind 7: step control and other small kernels,
+ *   kind 0: TT-rounding QR factor/apply, kind 1: TT-rounding SVD and
+ *   contractions (weno_tt_round).
  * ms and launches (host arrays of WENO_PROFILE_KINDS) receive the totals since
  * the last enable; *total_launches counts every kernel this handle launched
  * (graphs included) since the last enable. */
@@ -268,6 +269,52 @@ enum { WENO_CROSS_FP64_CHECK = 1 };
  * the next synchronising call returns WENO_ERR_ARG. */
 int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, const weno_fiber_set *sets,
                     int32_t n_sets, int32_t flags);
+
+/* ------------------------------------------------------------------------
+ * TT-rounding (Sec. 3, "TT-rounding": Oseledets' two-pass algorithm) of sums
+ * of 3D tensor trains, the operation that closes every stage of the TT time
+ * step, Eq. (tt-forward-euler) and Eq. (tt-ssprk3):
+ *   F = round(U^k + dt L(U^k)),   U' = round(a U^n + b F).
+ * ------------------------------------------------------------------------ */
+
+enum { WENO_TT_MAX_TERMS = 4, WENO_TT_MAX_RANK = 96 };
+
+/* One 3D TT in FP64 device memory: core[m] is shaped [n_m][r_{m-1}][r_m] with
+ * r_0 = r_3 = 1, X(i,j,k) = sum_{a,b} core[0][i][0][a] core[1][j][a][b] core[2][k][b][0]. */
+typedef struct {
+    int32_t n[3];
+    int32_t r[2];
+    double *core[3];
+} weno_tt3;
+
+/* out = round(sum_t coef[t] term[t], eps_tt) with ||sum - out||_F <= eps_tt ||sum||_F.
+ * Terms share n; their cores are read only.  out.core[m] are caller device
+ * buffers of cap[m] doubles; the call writes out.n, out.r (the ranks it chose)
+ * and norm (= ||sum||_F).  Sufficient capacities: with k3 = min(n3, R2),
+ * k2 = min(n2 k3, R1), kc = min(n1, k2), ke = min(kc n2, k3) (R1, R2 the summed
+ * ranks): cap = {n1 kc, n2 kc ke, n3 ke}. */
+typedef struct {
+    int32_t n_terms;
+    int32_t reserved;
+    double coef[WENO_TT_MAX_TERMS];
+    weno_tt3 term[WENO_TT_MAX_TERMS];
+    weno_tt3 out;
+    int64_t cap[3];
+    double norm;
+} weno_tt_round_problem;
+
+/* Rounds every problem of the batch (probs: HOST array; the ranks and norms
+ * are written back into it).  Right-to-left orthogonalisation by Householder
+ * QR of the core unfoldings, then left-to-right truncated SVDs (one-sided
+ * Jacobi of the triangular factors) with threshold eps_tt / sqrt(2) ||sum||_F,
+ * all in FP64 on the handle's stream.  The call synchronises the stream twice
+ * (to read the ranks it chose); the output cores are complete when the stream
+ * next synchronises.  Kernel timing kinds: 0 (QR factor/apply), 1 (SVD and
+ * contractions).  Errors: WENO_ERR_ARG for 0 or more than 4 terms, unequal
+ * mode sizes, null cores, ranks < 1, eps_tt < 0, or too small a capacity
+ * (nothing is written); WENO_ERR_UNSUPPORTED when the summed ranks R1 or R2
+ * exceed WENO_TT_MAX_RANK. */
+int weno_tt_round(weno_handle h, weno_tt_round_problem *probs, int32_t n_probs, double eps_tt);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ CROSS_FP64_CHECK = 1
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
            "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
            "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read",
-           "weno_sums_noalloc")
+           "weno_sums_noalloc", "weno_tt_round")
 PROFILE_KINDS = 8
 
 
@@ -55,6 +55,18 @@ class weno_fiber_set(C.Structure):
                 ("out", C.c_void_p)]
 
 
+class weno_tt3(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("r", C.c_int32 * 2), ("core", C.c_void_p * 3)]
+
+
+TT_MAX_TERMS, TT_MAX_RANK = 4, 96
+
+
+class weno_tt_round_problem(C.Structure):
+    _fields_ = [("n_terms", C.c_int32), ("reserved", C.c_int32), ("coef", C.c_double * TT_MAX_TERMS),
+                ("term", weno_tt3 * TT_MAX_TERMS), ("out", weno_tt3), ("cap", C.c_int64 * 3), ("norm", C.c_double)]
+
+
 _lib = None
 
 
@@ -84,6 +96,7 @@ def lib():
         L.weno_profile_enable.argtypes = [vp, i32]
         L.weno_profile_read.argtypes = [vp, P(d), P(i64), P(i64)]
         L.weno_sums_noalloc.argtypes = [vp, i32, i64, vp, vp]
+        L.weno_tt_round.argtypes = [vp, P(weno_tt_round_problem), i32, d]
         for name in EXPORTS:
             if name != "weno_last_error":
                 getattr(L, name).restype = C.c_int
@@ -227,6 +240,53 @@ def weno_profile_read(h):
     tot = C.c_int64()
     _check(h, lib().weno_profile_read(h, ms, n, C.byref(tot)))
     return list(ms), list(n), tot.value
+
+
+def tt_caps(n, R1, R2):
+    """Output capacities (doubles per core) that always suffice for a sum of summed ranks R1, R2."""
+    k3 = min(n[2], R2)
+    k2 = min(n[1] * k3, R1)
+    kc = min(n[0], k2)
+    ke = min(kc * n[1], k3)
+    return (n[0] * kc, n[1] * kc * ke, n[2] * ke)
+
+
+def weno_tt_round(h, problems, eps_tt):
+    """problems: list of term lists [(coef, [core0, core1, core2]), ...], cores FP64 CUDA
+    tensors shaped [n_m, r_{m-1}, r_m].  Returns [(cores, norm)] with the rounded cores
+    as CUDA tensors of the chosen ranks."""
+    import torch
+    arr = (weno_tt_round_problem * len(problems))()
+    keep = []
+    for i, terms in enumerate(problems):
+        P = arr[i]
+        P.n_terms = len(terms)
+        R1 = R2 = 0
+        for t, (c, cores) in enumerate(terms):
+            P.coef[t] = float(c)
+            X = P.term[t]
+            for m in range(3):
+                X.n[m] = int(cores[m].shape[0])
+                X.core[m] = _ptr(cores[m], torch.float64).value
+            X.r[0], X.r[1] = int(cores[0].shape[2]), int(cores[1].shape[2])
+            R1 += X.r[0]
+            R2 += X.r[1]
+        n = [int(terms[0][1][m].shape[0]) for m in range(3)]
+        caps = tt_caps(n, R1, R2)
+        bufs = [torch.empty(max(1, c), dtype=torch.float64, device="cuda") for c in caps]
+        keep.append(bufs)
+        for m in range(3):
+            P.out.core[m] = bufs[m].data_ptr()
+            P.cap[m] = caps[m]
+    _check(h, lib().weno_tt_round(h, arr, len(problems), float(eps_tt)))
+    out = []
+    for i, bufs in enumerate(keep):
+        o = arr[i].out
+        n, r1, r2 = list(o.n), o.r[0], o.r[1]
+        cores = [bufs[0][:n[0] * r1].view(n[0], 1, r1), bufs[1][:n[1] * r1 * r2].view(n[1], r1, r2),
+                 bufs[2][:n[2] * r2].view(n[2], r2, 1)]
+        out.append((cores, arr[i].norm))
+    return out
 
 
 def weno_cross_eval(h, instances, sets, fp64_check=False):
