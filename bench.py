@@ -313,18 +313,93 @@ def cross_flops(mode, fd, r, nm, n_left, n_right):
     return samples, samples * per
 
 
-def bench_cross(weno, I, torch, reps=10):
-    """The batched WENO-cross workload: 64 TT instances (n per mode from
-    {64,128,256,512}, ranks 2..32, TT-SVD of seeded smooth fields with a tanh
-    front), every sweep mode x flux direction (9 fiber sets per instance), all
-    evaluated in one persistent launch, FP32."""
-    insts, sets = [], []
-    samples = flops = 0
+def tt_workload(I, torch):
+    """The 64 seeded TT instances of the cross workload (n per mode from
+    {64,128,256,512}, ranks 2..32, TT-SVD of smooth fields with a tanh front),
+    FP32 cores on the GPU."""
+    insts = []
     for k in range(64):
         inst = I.tt_instance(seed=I.MASTER_SEED + k)
-        d = dict(n=inst["n"], r=inst["r"], h=[1.0 / x for x in inst["n"]], bc=((0, 0),) * 3, alpha=3.0,
-                 cores=[[torch.from_numpy(c).cuda() for c in fc] for fc in inst["cores"]])
-        insts.append(d)
+        insts.append(dict(n=inst["n"], r=inst["r"], h=[1.0 / x for x in inst["n"]], bc=((0, 0),) * 3, alpha=3.0,
+                          cores=[[torch.from_numpy(c).cuda() for c in fc] for fc in inst["cores"]]))
+    return insts
+
+
+def qr_flops(m, k):
+    """Householder QR of an m x k matrix, m >= k: 2 m k^2 - 2 k^3 / 3."""
+    k = min(m, k)
+    return 2.0 * m * k * k - 2.0 * k ** 3 / 3.0
+
+
+def qapply_flops(m, k, p):
+    """Q [X; 0] for a k x p block X with Q from an m x k Householder QR."""
+    k = min(m, k)
+    return 4.0 * m * k * p - 2.0 * k * k * p
+
+
+def tt_round_flops(n, R1, R2, r1, r2):
+    """Algorithmic FP64 flops of the QR factor and apply steps of one rounding."""
+    k3 = min(n[2], R2)
+    mB = n[1] * k3
+    k2 = min(mB, R1)
+    kc = min(n[0], k2)
+    f = qr_flops(n[2], R2) + qr_flops(mB, R1) + qr_flops(n[0], k2) + qr_flops(r1 * n[1], k3)
+    f += qapply_flops(n[0], k2, r1) + qapply_flops(mB, k2, r1)
+    f += qapply_flops(r1 * n[1], k3, r2) + qapply_flops(n[2], k3, r2)
+    return f
+
+
+def bench_tt(weno, torch, insts, reps=5, eps=1e-6, dt=1e-3):
+    """The forward-Euler rounding F = round(U + dt L, eps) of Eq. (tt-forward-euler)
+    for all 320 field TTs of the cross workload in one weno_tt_round call: U is a
+    field's TT, L stands in with the next field's TT of the same instance (same
+    modes and ranks), so the sums have ranks 2 r <= 64.  FP64."""
+    probs = []
+    for d in insts:
+        c64 = [[c.double().contiguous() for c in fc] for fc in d["cores"]]
+        for f in range(5):
+            probs.append([(1.0, c64[f]), (dt, c64[(f + 1) % 5])])
+    h = weno.weno_init(None)
+    for _ in range(2):
+        outs = weno.weno_tt_round(h, probs, eps)
+    weno.weno_sync(h)
+    weno.weno_profile_enable(h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        outs = weno.weno_tt_round(h, probs, eps)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    kms, kn, launches = weno.weno_profile_read(h)
+    weno.weno_destroy(h)
+    flops = 0.0
+    for terms, (cores, _) in zip(probs, outs):
+        n = [int(terms[0][1][m].shape[0]) for m in range(3)]
+        R1 = sum(int(c[0].shape[2]) for _, c in terms)
+        R2 = sum(int(c[1].shape[2]) for _, c in terms)
+        flops += tt_round_flops(n, R1, R2, int(cores[0].shape[2]), int(cores[1].shape[2]))
+    qr_ms = kms[0] / reps
+    achieved = flops / (qr_ms * 1e-3) / 1e12
+    return {"workload": "tt_forward_euler_round_320_fields", "value": len(probs) / (ms * 1e-3), "unit": "TT/s",
+            "ms_per_call": ms, "problems": len(probs), "eps_tt": eps, "dtype": "f64",
+            "kernels_ms_per_call": {"qr_factor_apply": qr_ms, "svd_and_contractions": kms[1] / reps},
+            "gpu_launches_per_call": launches / reps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None, "kernel": "k_qr_factor+k_qr_apply",
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                         "flops": "Householder 2mk^2-2k^3/3 per QR, 4mkp-2k^2p per Q apply"}}
+
+
+def bench_cross(weno, I, torch, insts, reps=10):
+    """The batched WENO-cross workload: the 64 TT instances, every sweep mode x
+    flux direction (9 fiber sets per instance), all evaluated in one persistent
+    launch, FP32."""
+    sets = []
+    samples = flops = 0
+    for k, d in enumerate(insts):
+        inst = d
         for mode in range(3):
             for fd in range(3):
                 left, right = I.cross_index_sets(1000 * k + 10 * mode + fd, inst["n"], inst["r"], mode)
@@ -414,6 +489,9 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
+    ap.add_argument("--only", choices=["cross", "tt", "scalar"],
+                    help="run one side measurement alone and print its JSON (for profiling)")
+    ap.add_argument("--reps", type=int, default=5, help="timed calls of the --only measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -433,6 +511,17 @@ def main():
     __graft_entry__.build()
     from paper_2405_12301_gb300 import inputs as I
     from paper_2405_12301_gb300 import weno
+
+    if args.only:
+        if args.only == "scalar":
+            print(json.dumps(bench_scalar(weno, I, torch)))
+            return
+        insts = tt_workload(I, torch)
+        if args.only == "cross":
+            print(json.dumps(bench_cross(weno, I, torch, insts, reps=args.reps)))
+        else:
+            print(json.dumps(bench_tt(weno, torch, insts, reps=args.reps)))
+        return
 
     w = WORKLOADS[args.workload]
     cells = 1
@@ -471,7 +560,9 @@ def main():
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
            "api": "weno_run_host (pinned host state, one step per call)"}
 
-    cross = bench_cross(weno, I, torch) if (rank == 0 and not args.no_cross) else None
+    insts = tt_workload(I, torch) if (rank == 0 and not args.no_cross) else None
+    cross = bench_cross(weno, I, torch, insts) if insts is not None else None
+    ttr = bench_tt(weno, torch, insts) if insts is not None else None
     acc = accuracy(weno, I, torch) if rank == 0 else None
     scalar = bench_scalar(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     rl = roofline(w, True, kms, kn, cells)
@@ -496,6 +587,7 @@ def main():
         "accuracy": acc,
         "cross_eval": cross,
         "scalar_advection": scalar,
+        "tt_round": ttr,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
