@@ -316,6 +316,29 @@ typedef struct {
  * exceed WENO_TT_MAX_RANK. */
 int weno_tt_round(weno_handle h, weno_tt_round_problem *probs, int32_t n_probs, double eps_tt);
 
+/* ------------------------------------------------------------------------
+ * Cross-index selection (Sec. 3, "TT-cross Interpolation": the rows and
+ * columns of the skeleton decompositions are chosen by the maximum-volume
+ * principle, Goreinov et al. 2010).
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t n, r;       /* n >= r, 1 <= r <= 64 */
+    const double *A;    /* device, n x r row-major */
+    double *B;          /* device, n x r: receives A A[I]^{-1} (identity on the rows I) */
+    int32_t *idx;       /* device, r: receives the selected rows I */
+} weno_maxvol_problem;
+
+/* Batched maxvol, FP64, one CTA per matrix: the r pivot rows of Gaussian
+ * elimination with partial pivoting, B = A A[I]^{-1}, then row swaps while
+ * some |B[i][j]| > 1 + delta (each swap multiplies |det A[I]| by |B[i][j]|;
+ * ties go to the first entry in row-major order) or max_iters swaps are done.
+ * probs: HOST array; synchronises the stream; swaps (host, may be NULL)
+ * receives the swaps per matrix.  Errors: WENO_ERR_ARG for bad sizes, null
+ * pointers, or a matrix whose pivot rows are singular (rank < r). */
+int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int32_t n_probs, double delta, int32_t max_iters,
+                int32_t *swaps);
+
 #ifdef __cplusplus
 }
 #endif

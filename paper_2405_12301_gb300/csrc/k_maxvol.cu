@@ -1,0 +1,197 @@
+// k_maxvol.cu -- batched maxvol (the maximum-volume row selection that picks
+// the cross indices of TT-cross, Sec. 3 "TT-cross Interpolation"), FP64, one
+// CTA per n x r matrix (r <= 64):
+//   1. the r pivot rows of Gaussian elimination with partial pivoting on a
+//      working copy W (largest remaining |W[i][j]| of column j, ties to the
+//      smaller row);
+//   2. B = A A[I]^{-1}, with A[I] inverted by Gauss-Jordan with partial
+//      pivoting in shared memory;
+//   3. while max |B[i][j]| > 1 + delta (ties to the first entry in row-major
+//      order): row i replaces I[j] and B -= B[:, j] (B[i, :] - e_j) / B[i][j].
+// W and B live in global memory (L2-resident); every pass is one block-wide
+// argmax and one row-parallel update.
+#include <climits>
+
+#include "weno_dev.cuh"
+#include "weno_internal.h"
+
+namespace wg {
+
+constexpr int MV_NT = 256, MV_NW = MV_NT / 32;
+
+// Block-wide argmax of (v, i): largest v, smallest i among equal v.  Every
+// thread gets the winner.  v must be >= 0 or -1 (excluded).
+__device__ __forceinline__ void block_argmax(double &v, long long &i, double *sv, long long *si)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const long long oi = __shfl_xor_sync(0xFFFFFFFFu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();  // earlier readers of sv/si are done
+    if (lane == 0) {
+        sv[warp] = v;
+        si[warp] = i;
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    for (int w = 1; w < MV_NW; ++w)
+        if (sv[w] > v || (sv[w] == v && si[w] < i)) {
+            v = sv[w];
+            i = si[w];
+        }
+}
+
+size_t maxvol_smem(int r) { return sizeof(double) * (size_t)r * (2 * r + 1) + sizeof(int) * (size_t)(r + 1); }
+
+__global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, double delta, int max_iters)
+{
+    const MaxvolDesc d = descs[blockIdx.x];
+    const int n = d.n, r = d.r;
+    extern __shared__ double sm[];
+    double *G = sm;                                  // [r][2r]: [A[I] | identity] for Gauss-Jordan
+    double *row = G + (size_t)r * 2 * r;             // [r]
+    int *I = reinterpret_cast<int *>(row + r);       // [r]
+    __shared__ double sv[MV_NW];
+    __shared__ long long si[MV_NW];
+    __shared__ int s_fail;
+    double *W = d.W, *B = d.B;
+    const long long nr = (long long)n * r;
+    if (threadIdx.x == 0) s_fail = 0;
+    for (long long e = threadIdx.x; e < nr; e += MV_NT) W[e] = d.A[e];
+    __syncthreads();
+
+    // 1. partial pivoting (rows already chosen are looked up in I)
+    for (int j = 0; j < r; ++j) {
+        double v = -1.0;
+        long long bi = LLONG_MAX;
+        for (int i = threadIdx.x; i < n; i += MV_NT) {
+            bool chosen = false;
+            for (int t = 0; t < j; ++t) chosen |= (I[t] == i);
+            const double a = chosen ? -1.0 : fabs(W[(long long)i * r + j]);
+            if (a > v || (a == v && i < bi)) {
+                v = a;
+                bi = i;
+            }
+        }
+        block_argmax(v, bi, sv, si);
+        const int p = (int)bi;
+        if (threadIdx.x == 0) I[j] = p;
+        __syncthreads();
+        const double wp = W[(long long)p * r + j];
+        if (wp != 0.0) {
+            for (int i = threadIdx.x; i < n; i += MV_NT) {
+                bool chosen = false;
+                for (int t = 0; t <= j; ++t) chosen |= (I[t] == i);
+                if (chosen) continue;
+                double *wi = W + (long long)i * r;
+                const double f = wi[j] / wp;
+                for (int c = 0; c < r; ++c) wi[c] = fma(-f, W[(long long)p * r + c], wi[c]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // 2. B = A A[I]^{-1}: Gauss-Jordan on [A[I] | identity]
+    for (int e = threadIdx.x; e < r * 2 * r; e += MV_NT) {
+        const int i = e / (2 * r), c = e - i * 2 * r;
+        G[e] = c < r ? d.A[(long long)I[i] * r + c] : (c - r == i ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int c = 0; c < r; ++c) {
+        if (threadIdx.x == 0) {
+            int p = c;
+            double best = fabs(G[c * 2 * r + c]);
+            for (int i = c + 1; i < r; ++i)
+                if (fabs(G[i * 2 * r + c]) > best) {
+                    best = fabs(G[i * 2 * r + c]);
+                    p = i;
+                }
+            if (best == 0.0) s_fail = 1;
+            if (p != c)
+                for (int t = 0; t < 2 * r; ++t) {
+                    const double x = G[c * 2 * r + t];
+                    G[c * 2 * r + t] = G[p * 2 * r + t];
+                    G[p * 2 * r + t] = x;
+                }
+            const double inv = best == 0.0 ? 0.0 : 1.0 / G[c * 2 * r + c];
+            for (int t = 0; t < 2 * r; ++t) G[c * 2 * r + t] *= inv;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < r; i += MV_NT) row[i] = G[i * 2 * r + c];  // multipliers, read before any write
+        __syncthreads();
+        for (int e = threadIdx.x; e < r * 2 * r; e += MV_NT) {
+            const int i = e / (2 * r), t = e - i * 2 * r;
+            if (i == c) continue;
+            G[e] = fma(-row[i], G[c * 2 * r + t], G[e]);
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (threadIdx.x == 0) d.status[0] = 1;
+        return;
+    }
+    for (long long e = threadIdx.x; e < nr; e += MV_NT) {
+        const long long i = e / r;
+        const int c = (int)(e - i * r);
+        const double *ai = d.A + i * r;
+        double s = 0.0;
+        for (int k = 0; k < r; ++k) s = fma(ai[k], G[k * 2 * r + r + c], s);
+        B[e] = s;
+    }
+    __syncthreads();
+
+    // 3. swaps
+    int it = 0;
+    for (; it < max_iters; ++it) {
+        double v = -1.0;
+        long long bi = LLONG_MAX;
+        for (long long e = threadIdx.x; e < nr; e += MV_NT) {
+            const double a = fabs(B[e]);
+            if (a > v) {  // e grows per thread, so equal values keep the first
+                v = a;
+                bi = e;
+            }
+        }
+        block_argmax(v, bi, sv, si);
+        if (!(v > 1.0 + delta)) break;
+        const int i0 = (int)(bi / r), j0 = (int)(bi - (long long)i0 * r);
+        for (int c = threadIdx.x; c < r; c += MV_NT) row[c] = B[(long long)i0 * r + c] - (c == j0 ? 1.0 : 0.0);
+        __syncthreads();
+        const double piv = row[j0] + 1.0;
+        for (int i = threadIdx.x; i < n; i += MV_NT) {
+            double *bi_ = B + (long long)i * r;
+            const double f = bi_[j0] / piv;
+            for (int c = 0; c < r; ++c) bi_[c] = fma(-f, row[c], bi_[c]);
+        }
+        if (threadIdx.x == 0) I[j0] = i0;
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < r; j += MV_NT) d.idx[j] = I[j];
+    if (threadIdx.x == 0) {
+        d.status[0] = 0;
+        d.swaps[0] = it;
+    }
+}
+
+cudaError_t launch_maxvol(const MaxvolDesc *d, int n, int max_r, double delta, int max_iters, cudaStream_t s)
+{
+    const size_t smem = maxvol_smem(max_r);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_maxvol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)maxvol_smem(MV_RMAX));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_maxvol<<<n, MV_NT, smem, s>>>(d, delta, max_iters);
+    return cudaGetLastError();
+}
+
+}  // namespace wg

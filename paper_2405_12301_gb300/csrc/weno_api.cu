@@ -38,6 +38,9 @@ struct weno_ctx {
     // TT-rounding scratch
     void *tbuf = nullptr;
     size_t tbuf_bytes = 0;
+    // maxvol / TT-cross scratch
+    void *mbuf = nullptr;
+    size_t mbuf_bytes = 0;
     // kernel timing (weno_profile_*)
     struct EvPair { cudaEvent_t a, b; int kind; };
     bool prof = false;
@@ -135,6 +138,7 @@ static void free_all(weno_ctx *h)
     cudaFree(h->ctl);
     cudaFree(h->xbuf);
     cudaFree(h->tbuf);
+    cudaFree(h->mbuf);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->capture) cudaStreamDestroy(h->capture);
     for (auto &ev : h->pending) {
@@ -1057,6 +1061,62 @@ extern "C" int weno_tt_round(weno_handle h, weno_tt_round_problem *probs, int32_
         o.r[0] = pl[i].r1;
         o.r[1] = pl[i].r2;
         probs[i].norm = norms[2 * i + 1];
+    }
+    return WENO_OK;
+}
+
+// ------------------------------------------------------------------ maxvol
+
+static int grow(weno_ctx *h, void **buf, size_t *have, size_t bytes)
+{
+    if (bytes <= *have) return WENO_OK;
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    CK(h, cudaMalloc(buf, bytes));
+    *have = bytes;
+    return WENO_OK;
+}
+
+extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int32_t n_probs, double delta,
+                           int32_t max_iters, int32_t *swaps)
+{
+    if (!h) return WENO_ERR_ARG;
+    if (!probs || n_probs < 1) return fail(h, WENO_ERR_ARG, "weno_maxvol: empty input");
+    if (!(delta >= 0.0) || max_iters < 0) return fail(h, WENO_ERR_ARG, "weno_maxvol: need delta >= 0, max_iters >= 0");
+    std::vector<MaxvolDesc> ds(n_probs);
+    size_t w_total = 0;
+    int max_r = 1;
+    for (int i = 0; i < n_probs; ++i) {
+        const weno_maxvol_problem &P = probs[i];
+        if (P.r < 1 || P.r > MV_RMAX || P.n < P.r || !P.A || !P.B || !P.idx)
+            return fail(h, WENO_ERR_ARG, "weno_maxvol: need 1 <= r <= 64, n >= r and non-null A, B, idx");
+        w_total += (((size_t)P.n * P.r + 31) & ~size_t(31));
+        max_r = std::max(max_r, (int)P.r);
+    }
+    const size_t off_desc = 0;
+    const size_t off_int = (sizeof(MaxvolDesc) * n_probs + 255) & ~size_t(255);
+    const size_t off_w = (off_int + sizeof(int) * 2 * n_probs + 255) & ~size_t(255);
+    int r = grow(h, &h->mbuf, &h->mbuf_bytes, off_w + sizeof(double) * w_total);
+    if (r) return r;
+    char *base = (char *)h->mbuf;
+    int *ints = (int *)(base + off_int);
+    double *w = (double *)(base + off_w);
+    for (int i = 0; i < n_probs; ++i) {
+        const weno_maxvol_problem &P = probs[i];
+        ds[i] = MaxvolDesc{P.A, P.B, w, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
+        w += (((size_t)P.n * P.r + 31) & ~size_t(31));
+    }
+    MaxvolDesc *dd = (MaxvolDesc *)(base + off_desc);
+    CK(h, cudaMemcpyAsync(dd, ds.data(), sizeof(MaxvolDesc) * n_probs, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, n_probs, max_r, delta, max_iters, h->stream); }));
+    std::vector<int> st(2 * n_probs);
+    CK(h, cudaMemcpyAsync(st.data(), ints, sizeof(int) * 2 * n_probs, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < n_probs; ++i) {
+        if (st[2 * i]) return fail(h, WENO_ERR_ARG, "weno_maxvol: the pivot rows of a matrix are singular (rank < r)");
+        if (swaps) swaps[i] = st[2 * i + 1];
     }
     return WENO_OK;
 }

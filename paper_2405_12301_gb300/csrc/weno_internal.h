@@ -171,4 +171,19 @@ cudaError_t launch_tt_build(const TTSumDesc *d, int n, cudaStream_t s);
 cudaError_t launch_tt_contract(const TTSumDesc *d, int n, cudaStream_t s);
 cudaError_t launch_tt_gemm_tr(const GemmDesc *d, int n, cudaStream_t s);
 
+
+// ---- batched maxvol (k_maxvol.cu)
+constexpr int MV_RMAX = 64;
+struct MaxvolDesc {
+    const double *A;   // n x r row-major
+    double *B;         // n x r: A A[I]^{-1} on exit
+    double *W;         // n x r scratch
+    int *idx;          // r selected rows
+    int *status;       // 0 ok, 1 A[I] singular after pivoting
+    int *swaps;
+    int n, r;
+};
+size_t maxvol_smem(int r);
+cudaError_t launch_maxvol(const MaxvolDesc *d, int n, int max_r, double delta, int max_iters, cudaStream_t s);
+
 }  // namespace wg

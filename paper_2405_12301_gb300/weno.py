@@ -22,7 +22,7 @@ CROSS_FP64_CHECK = 1
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
            "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
            "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read",
-           "weno_sums_noalloc", "weno_tt_round")
+           "weno_sums_noalloc", "weno_tt_round", "weno_maxvol")
 PROFILE_KINDS = 8
 
 
@@ -67,6 +67,10 @@ class weno_tt_round_problem(C.Structure):
                 ("term", weno_tt3 * TT_MAX_TERMS), ("out", weno_tt3), ("cap", C.c_int64 * 3), ("norm", C.c_double)]
 
 
+class weno_maxvol_problem(C.Structure):
+    _fields_ = [("n", C.c_int32), ("r", C.c_int32), ("A", C.c_void_p), ("B", C.c_void_p), ("idx", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -97,6 +101,7 @@ def lib():
         L.weno_profile_read.argtypes = [vp, P(d), P(i64), P(i64)]
         L.weno_sums_noalloc.argtypes = [vp, i32, i64, vp, vp]
         L.weno_tt_round.argtypes = [vp, P(weno_tt_round_problem), i32, d]
+        L.weno_maxvol.argtypes = [vp, P(weno_maxvol_problem), i32, d, i32, P(i32)]
         for name in EXPORTS:
             if name != "weno_last_error":
                 getattr(L, name).restype = C.c_int
@@ -287,6 +292,25 @@ def weno_tt_round(h, problems, eps_tt):
                  bufs[2][:n[2] * r2].view(n[2], r2, 1)]
         out.append((cores, arr[i].norm))
     return out
+
+
+def weno_maxvol(h, mats, delta=1e-2, max_iters=200):
+    """mats: FP64 CUDA tensors n x r.  Returns [(idx int32 tensor, B tensor, swaps)]."""
+    import torch
+    arr = (weno_maxvol_problem * len(mats))()
+    outs = []
+    for i, A in enumerate(mats):
+        n, r = A.shape
+        B = torch.empty_like(A)
+        idx = torch.empty(r, dtype=torch.int32, device=A.device)
+        arr[i].n, arr[i].r = n, r
+        arr[i].A = _ptr(A, torch.float64).value
+        arr[i].B = B.data_ptr()
+        arr[i].idx = idx.data_ptr()
+        outs.append((idx, B))
+    sw = (C.c_int32 * len(mats))()
+    _check(h, lib().weno_maxvol(h, arr, len(mats), float(delta), int(max_iters), sw))
+    return [(idx, B, int(sw[i])) for i, (idx, B) in enumerate(outs)]
 
 
 def weno_cross_eval(h, instances, sets, fp64_check=False):
