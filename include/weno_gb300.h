@@ -339,6 +339,34 @@ typedef struct {
 int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int32_t n_probs, double delta, int32_t max_iters,
                 int32_t *swaps);
 
+/* One fixed-rank TT-cross of A(i, j, k, f) = the flux_dir residual contribution
+ * -(F^_{i+1/2} - F^_{i-1/2}) / h of Euler component f at cell (i, j, k) of one
+ * weno_tt_instance (the values weno_cross_eval computes).  The components sit
+ * in the last core, as in the LF-cross layout of Sec. 4.2. */
+typedef struct {
+    int32_t r[2];       /* cross ranks: 1 <= r1 <= min(n1, n2 r2, 64), 1 <= r2 <= min(r1 n2, 5 n3, 64) */
+    int32_t *J1;        /* device [r1][3] (j, k, f): initial right index set in, final one out */
+    int32_t *J2;        /* device [r2][2] (k, f): in/out */
+    int32_t *I1;        /* device [r1]: left index set out */
+    int32_t *I2;        /* device [r2][2] (i, j): out */
+    double *core[3];    /* device out: [n1][1][r1], [n2][r1][r2], [n3][r2][5] */
+} weno_tt_cross_problem;
+
+/* Alternating TT-cross with maxvol index selection (Sec. 3, "TT-cross
+ * Interpolation"; AMEn's rank adaptation is not part of it).  For every
+ * instance i (problem i): a left-to-right pass evaluates A(:, J1), A(I1, :, J2),
+ * A(I2, :, :) as fiber sets, takes the Householder Q of each unfolding and
+ * maxvol's rows of Q to form I1, I2 and the interpolation cores Q Q[I]^{-1};
+ * `sweeps` times a right-to-left pass updates J2 and J1 the same way before the
+ * next left-to-right pass.  The resulting TT interpolates A on the final index
+ * sets.  Fibers are evaluated in FP32 (FP64 with WENO_CROSS_FP64_CHECK in
+ * flags); the selection and the cores are FP64.  inst, probs: HOST arrays;
+ * synchronises once at the end.  Uses the handle's gamma and eps_weno.
+ * Errors: WENO_ERR_ARG for bad ranks, null pointers or a fiber matrix of rank
+ * below the cross rank; those of weno_cross_eval. */
+int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, int32_t flux_dir,
+                  weno_tt_cross_problem *probs, int32_t sweeps, double delta, int32_t flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
     const int nsub = (int)((r1 - r0 + b - 1) / b);
     const int b1 = (int)min((long long)b, r1 - r0);
     const int kk = min(b1, k);  // rows of X (k unless the chunk is shorter than k)
-    const double *Xin = d.X + (long long)chunk * d.x_chunk_stride;
+    const double *Xin = d.X ? d.X + (long long)chunk * d.x_chunk_stride : nullptr;  // null: identity
     for (int e = threadIdx.x; e < kk * p; e += TT_NT) {
         const int j = e / p, q = e - j * p;
-        X[q * ldx + j] = Xin[(long long)j * d.ldx + q];
+        X[q * ldx + j] = Xin ? Xin[(long long)j * d.ldx + q] : (j == q ? 1.0 : 0.0);
     }
     __syncthreads();
     auto store = [&](long long row0, int rows) {

@@ -41,6 +41,8 @@ struct weno_ctx {
     // maxvol / TT-cross scratch
     void *mbuf = nullptr;
     size_t mbuf_bytes = 0;
+    void *cbuf = nullptr;
+    size_t cbuf_bytes = 0;
     // kernel timing (weno_profile_*)
     struct EvPair { cudaEvent_t a, b; int kind; };
     bool prof = false;
@@ -139,6 +141,7 @@ static void free_all(weno_ctx *h)
     cudaFree(h->xbuf);
     cudaFree(h->tbuf);
     cudaFree(h->mbuf);
+    cudaFree(h->cbuf);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     if (h->capture) cudaStreamDestroy(h->capture);
     for (auto &ev : h->pending) {
@@ -1118,5 +1121,243 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
         if (st[2 * i]) return fail(h, WENO_ERR_ARG, "weno_maxvol: the pivot rows of a matrix are singular (rank < r)");
         if (swaps) swaps[i] = st[2 * i + 1];
     }
+    return WENO_OK;
+}
+
+// ---------------------------------------------------------------- TT-cross
+// weno_tt_cross: fixed-rank alternating TT-cross of A(i, j, k, f), the flux_dir
+// residual contribution of component f of each TT instance (evaluated on
+// fibers by weno_cross_eval), with maxvol selecting the index sets.  Every
+// step is batched over the instances and runs on the handle's stream without
+// a host round trip; the call synchronises once at the end to read maxvol's
+// status words.
+
+namespace {
+struct XProb {
+    int n[3] = {0, 0, 0};
+    int r1 = 0, r2 = 0;
+    void *outL0 = nullptr, *outL1 = nullptr, *outL2 = nullptr;
+    int *right0 = nullptr, *left1 = nullptr, *right1 = nullptr, *left2 = nullptr;
+    double *M0 = nullptr, *M1 = nullptr, *MR2 = nullptr, *MR1 = nullptr;
+    double *Q0 = nullptr, *Q1 = nullptr, *QR2 = nullptr, *QR1 = nullptr;
+    double *B1 = nullptr, *BR = nullptr, *Wmv = nullptr;
+    int *idx = nullptr;
+    QRPlan q0, q1, qr2, qr1;
+};
+}  // namespace
+
+extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, int32_t flux_dir,
+                             weno_tt_cross_problem *probs, int32_t sweeps, double delta, int32_t flags)
+{
+    if (!h) return WENO_ERR_ARG;
+    if (!inst || !probs || n_inst < 1 || n_inst > 65535) return fail(h, WENO_ERR_ARG, "weno_tt_cross: need 1..65535 instances");
+    if (flux_dir < 0 || flux_dir > 2 || sweeps < 0 || sweeps > 64 || !(delta >= 0.0))
+        return fail(h, WENO_ERR_ARG, "weno_tt_cross: need flux_dir 0..2, sweeps 0..64, delta >= 0");
+    const bool fp64 = (flags & WENO_CROSS_FP64_CHECK) != 0;
+    const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+    const int np = n_inst;
+    std::vector<XProb> xp(np);
+    int max_r = 1;
+    for (int i = 0; i < np; ++i) {
+        XProb &x = xp[i];
+        const weno_tt_cross_problem &P = probs[i];
+        for (int m = 0; m < 3; ++m) x.n[m] = inst[i].n[m];
+        x.r1 = P.r[0];
+        x.r2 = P.r[1];
+        const long long n1 = x.n[0], n2 = x.n[1], n3 = x.n[2];
+        if (x.r1 < 1 || x.r1 > MV_RMAX || x.r1 > n1 || x.r1 > 5 * n2 * n3 || x.r2 < 1 || x.r2 > MV_RMAX ||
+            x.r2 > (long long)x.r1 * n2 || x.r2 > 5 * n3 || x.r1 > n2 * x.r2)
+            return fail(h, WENO_ERR_ARG, "weno_tt_cross: need 1 <= r1 <= min(n1, n2 r2, 64), 1 <= r2 <= min(r1 n2, 5 n3, 64)");
+        if (!P.J1 || !P.J2 || !P.I1 || !P.I2 || !P.core[0] || !P.core[1] || !P.core[2])
+            return fail(h, WENO_ERR_ARG, "weno_tt_cross: null index set or core");
+        max_r = std::max({max_r, x.r1, x.r2});
+        qr_plan(x.q0, n1, x.r1);
+        qr_plan(x.q1, (long long)x.r1 * n2, x.r2);
+        qr_plan(x.qr2, 5 * n3, x.r2);
+        qr_plan(x.qr1, n2 * x.r2, x.r1);
+    }
+    const int n_mv = 2 * (sweeps + 1) + 2 * sweeps;  // maxvol calls of the whole run
+    const int NSLOT = 6;
+    const size_t dsz = std::max({sizeof(QRDesc), sizeof(QApplyDesc), sizeof(MaxvolDesc), sizeof(CrossDrvDesc)});
+    auto layout = [&](Bump &bp) -> char * {
+        char *desc = bp.take<char>(dsz * NSLOT * 2 * (size_t)np);
+        for (auto &x : xp) {
+            const size_t n1 = x.n[0], n2 = x.n[1], n3 = x.n[2], r1 = x.r1, r2 = x.r2;
+            x.outL0 = bp.take<char>(esz * 5 * n1 * r1);
+            x.outL1 = bp.take<char>(esz * 5 * r1 * n2 * r2);
+            x.outL2 = bp.take<char>(esz * 5 * r2 * n3);
+            x.right0 = bp.take<int>(2 * r1);
+            x.left1 = bp.take<int>(r1);
+            x.right1 = bp.take<int>(r2);
+            x.left2 = bp.take<int>(2 * r2);
+            x.M0 = bp.take<double>(n1 * r1);
+            x.M1 = bp.take<double>(r1 * n2 * r2);
+            x.MR2 = bp.take<double>(5 * n3 * r2);
+            x.MR1 = bp.take<double>(n2 * r2 * r1);
+            x.Q0 = bp.take<double>(n1 * r1);
+            x.Q1 = bp.take<double>(r1 * n2 * r2);
+            x.QR2 = bp.take<double>(5 * n3 * r2);
+            x.QR1 = bp.take<double>(n2 * r2 * r1);
+            x.B1 = bp.take<double>(r1 * n2 * r2);
+            const size_t mk = std::max({n1 * r1, r1 * n2 * r2, 5 * n3 * r2, n2 * r2 * r1});
+            x.BR = bp.take<double>(mk);
+            x.Wmv = bp.take<double>(mk);
+            x.idx = bp.take<int>(std::max(r1, r2));
+            qr_take(bp, x.q0);
+            qr_take(bp, x.q1);
+            qr_take(bp, x.qr2);
+            qr_take(bp, x.qr1);
+        }
+        return desc;
+    };
+    Bump count;
+    layout(count);
+    const size_t st_off = (count.off + 255) & ~size_t(255);
+    int r = grow(h, &h->cbuf, &h->cbuf_bytes, st_off + sizeof(int) * 2 * (size_t)n_mv * np);
+    if (r) return r;
+    Bump bp;
+    bp.base = (char *)h->cbuf;
+    char *desc = layout(bp);
+    int *status = (int *)((char *)h->cbuf + st_off);
+    auto slot = [&](int k) { return desc + dsz * 2 * (size_t)np * k; };
+    CK(h, cudaMemsetAsync(status, 0, sizeof(int) * 2 * (size_t)n_mv * np, h->stream));
+
+    std::vector<CrossDrvDesc> cd(np);
+    auto drv = [&](int kind, auto &&fill) -> int {
+        for (int i = 0; i < np; ++i) {
+            XProb &x = xp[i];
+            const weno_tt_cross_problem &P = probs[i];
+            CrossDrvDesc &c = cd[i];
+            c = CrossDrvDesc{};
+            for (int m = 0; m < 3; ++m) c.n[m] = x.n[m];
+            c.r1 = x.r1;
+            c.r2 = x.r2;
+            c.fp64 = fp64 ? 1 : 0;
+            c.I1 = P.I1;
+            c.I2 = P.I2;
+            c.J1 = P.J1;
+            c.J2 = P.J2;
+            c.idx = x.idx;
+            fill(x, P, c);
+        }
+        CrossDrvDesc *dd = (CrossDrvDesc *)slot(0);
+        CK(h, cudaMemcpyAsync(dd, cd.data(), sizeof(CrossDrvDesc) * np, cudaMemcpyHostToDevice, h->stream));
+        CK(h, launch(h, 1, h->stream, [&] { return launch_cross_drv(dd, np, kind, h->stream); }));
+        return WENO_OK;
+    };
+    auto evaluate = [&](int mode) -> int {
+        std::vector<weno_fiber_set> fs(np);
+        for (int i = 0; i < np; ++i) {
+            XProb &x = xp[i];
+            weno_fiber_set &f = fs[i];
+            f = weno_fiber_set{};
+            f.instance = i;
+            f.mode = mode;
+            f.flux_dir = flux_dir;
+            if (mode == 0) { f.n_left = 1; f.left = nullptr; f.n_right = x.r1; f.right = x.right0; f.out = x.outL0; }
+            if (mode == 1) { f.n_left = x.r1; f.left = x.left1; f.n_right = x.r2; f.right = x.right1; f.out = x.outL1; }
+            if (mode == 2) { f.n_left = x.r2; f.left = x.left2; f.n_right = 1; f.right = nullptr; f.out = x.outL2; }
+        }
+        return weno_cross_eval(h, inst, np, fs.data(), np, fp64 ? WENO_CROSS_FP64_CHECK : 0);
+    };
+    int mv_call = 0;
+    // QR (explicit Q) of every problem's matrix for this step, then maxvol on Q
+    auto select = [&](QRPlan XProb::*qp, double *XProb::*Mp, double *XProb::*Qp, double *XProb::*Bp,
+                      bool b_is_core0) -> int {
+        std::vector<QRPlan *> ps;
+        std::vector<ApplyReq> ar(np);
+        std::vector<MaxvolDesc> md(np);
+        for (int i = 0; i < np; ++i) {
+            XProb &x = xp[i];
+            QRPlan &q = x.*qp;
+            q.A = x.*Mp;
+            ps.push_back(&q);
+        }
+        int rr = tt_factor(h, ps, (QRDesc *)slot(1));
+        if (rr) return rr;
+        for (int i = 0; i < np; ++i) {
+            XProb &x = xp[i];
+            QRPlan &q = x.*qp;
+            // explicit Q (m x k): apply to the identity, row-major; the chunk stack reuses W
+            ar[i] = ApplyReq{&q, nullptr, q.k, q.k, x.Wmv, x.*Qp, q.m, q.k, 0, 1};
+        }
+        if ((rr = tt_apply(h, ar, (QApplyDesc *)slot(2)))) return rr;
+        int mr = 1;
+        for (int i = 0; i < np; ++i) {
+            XProb &x = xp[i];
+            QRPlan &q = x.*qp;
+            double *Bout = b_is_core0 ? probs[i].core[0] : x.*Bp;
+            int *st = status + 2 * ((size_t)mv_call * np + i);
+            md[i] = MaxvolDesc{x.*Qp, Bout, x.Wmv, x.idx, st, st + 1, (int)q.m, q.k};
+            mr = std::max(mr, q.k);
+        }
+        MaxvolDesc *dd = (MaxvolDesc *)slot(3);
+        CK(h, cudaMemcpyAsync(dd, md.data(), sizeof(MaxvolDesc) * np, cudaMemcpyHostToDevice, h->stream));
+        CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, np, mr, delta, 200, h->stream); }));
+        ++mv_call;
+        return WENO_OK;
+    };
+    auto nofill = [](XProb &, const weno_tt_cross_problem &, CrossDrvDesc &) {};
+    for (int it = 0; it <= sweeps; ++it) {
+        // ---- left to right
+        if ((r = drv(XD_PREP_L0, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) { c.right = x.right0; })))
+            return r;
+        if ((r = evaluate(0))) return r;
+        if ((r = drv(XD_GATHER_L0, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
+                 c.out = x.outL0;
+                 c.M = x.M0;
+             })))
+            return r;
+        if ((r = select(&XProb::q0, &XProb::M0, &XProb::Q0, &XProb::BR, true))) return r;
+        if ((r = drv(XD_UPDATE_L0, nofill))) return r;
+        if ((r = drv(XD_PREP_L1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
+                 c.left = x.left1;
+                 c.right = x.right1;
+             })))
+            return r;
+        if ((r = evaluate(1))) return r;
+        if ((r = drv(XD_GATHER_L1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
+                 c.out = x.outL1;
+                 c.M = x.M1;
+             })))
+            return r;
+        if ((r = select(&XProb::q1, &XProb::M1, &XProb::Q1, &XProb::B1, false))) return r;
+        if ((r = drv(XD_UPDATE_L1, [](XProb &x, const weno_tt_cross_problem &P, CrossDrvDesc &c) {
+                 c.B = x.B1;
+                 c.core = P.core[1];
+             })))
+            return r;
+        if ((r = drv(XD_PREP_L2, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) { c.left = x.left2; })))
+            return r;
+        if ((r = evaluate(2))) return r;
+        if ((r = drv(XD_GATHER_L2, [](XProb &x, const weno_tt_cross_problem &P, CrossDrvDesc &c) {
+                 c.out = x.outL2;
+                 c.M = x.MR2;
+                 c.core = P.core[2];
+             })))
+            return r;
+        if (it == sweeps) break;
+        // ---- right to left
+        if ((r = select(&XProb::qr2, &XProb::MR2, &XProb::QR2, &XProb::BR, false))) return r;
+        if ((r = drv(XD_UPDATE_R2, nofill))) return r;
+        if ((r = drv(XD_PREP_L1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
+                 c.left = x.left1;
+                 c.right = x.right1;
+             })))
+            return r;
+        if ((r = evaluate(1))) return r;
+        if ((r = drv(XD_GATHER_R1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
+                 c.out = x.outL1;
+                 c.M = x.MR1;
+             })))
+            return r;
+        if ((r = select(&XProb::qr1, &XProb::MR1, &XProb::QR1, &XProb::BR, false))) return r;
+        if ((r = drv(XD_UPDATE_R1, nofill))) return r;
+    }
+    std::vector<int> st(2 * (size_t)n_mv * np);
+    CK(h, cudaMemcpyAsync(st.data(), status, sizeof(int) * st.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k < st.size(); k += 2)
+        if (st[k]) return fail(h, WENO_ERR_ARG, "weno_tt_cross: a fiber matrix had rank below the cross rank");
     return WENO_OK;
 }

@@ -186,4 +186,25 @@ struct MaxvolDesc {
 size_t maxvol_smem(int r);
 cudaError_t launch_maxvol(const MaxvolDesc *d, int n, int max_r, double delta, int max_iters, cudaStream_t s);
 
+
+// ---- TT-cross sweep bookkeeping (k_cross_drv.cu)
+enum XdKind {
+    XD_PREP_L0, XD_PREP_L1, XD_PREP_L2,
+    XD_GATHER_L0, XD_GATHER_L1, XD_GATHER_L2, XD_GATHER_R1,
+    XD_UPDATE_L0, XD_UPDATE_L1, XD_UPDATE_R2, XD_UPDATE_R1
+};
+struct CrossDrvDesc {
+    int n[3];
+    int r1, r2;
+    int fp64;            // fiber values are double (else float)
+    const void *out;     // fiber-set output [5][n_left][n_mode][n_right]
+    double *M;           // gathered matrix
+    double *core;        // output core written by a gather / update
+    const int *idx;      // rows maxvol selected
+    const double *B;     // maxvol's A A[I]^{-1}
+    int *I1, *I2, *J1, *J2;
+    int *left, *right;   // fiber-set index arrays
+};
+cudaError_t launch_cross_drv(const CrossDrvDesc *d, int n, int kind, cudaStream_t s);
+
 }  // namespace wg

@@ -22,7 +22,7 @@ CROSS_FP64_CHECK = 1
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
            "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
            "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read",
-           "weno_sums_noalloc", "weno_tt_round", "weno_maxvol")
+           "weno_sums_noalloc", "weno_tt_round", "weno_maxvol", "weno_tt_cross")
 PROFILE_KINDS = 8
 
 
@@ -102,6 +102,7 @@ def lib():
         L.weno_sums_noalloc.argtypes = [vp, i32, i64, vp, vp]
         L.weno_tt_round.argtypes = [vp, P(weno_tt_round_problem), i32, d]
         L.weno_maxvol.argtypes = [vp, P(weno_maxvol_problem), i32, d, i32, P(i32)]
+        L.weno_tt_cross.argtypes = [vp, P(weno_tt_instance), i32, i32, P(weno_tt_cross_problem), i32, d, i32]
         for name in EXPORTS:
             if name != "weno_last_error":
                 getattr(L, name).restype = C.c_int
@@ -313,9 +314,7 @@ def weno_maxvol(h, mats, delta=1e-2, max_iters=200):
     return [(idx, B, int(sw[i])) for i, (idx, B) in enumerate(outs)]
 
 
-def weno_cross_eval(h, instances, sets, fp64_check=False):
-    """instances: list of dict(n, r, cores=[5][3] CUDA float32 tensors, h, alpha, bc);
-    sets: list of dict(instance, mode, flux_dir, left, right, out) with CUDA tensors."""
+def _instances(instances):
     import torch
     inst = (weno_tt_instance * len(instances))()
     for k, d in enumerate(instances):
@@ -329,6 +328,14 @@ def weno_cross_eval(h, instances, sets, fp64_check=False):
             for m in range(3):
                 inst[k].core[f][m] = _ptr(d["cores"][f][m], torch.float32).value
         inst[k].alpha = float(d["alpha"])
+    return inst
+
+
+def weno_cross_eval(h, instances, sets, fp64_check=False):
+    """instances: list of dict(n, r, cores=[5][3] CUDA float32 tensors, h, alpha, bc);
+    sets: list of dict(instance, mode, flux_dir, left, right, out) with CUDA tensors."""
+    import torch
+    inst = _instances(instances)
     fs = (weno_fiber_set * len(sets))()
     for k, s in enumerate(sets):
         fs[k].instance, fs[k].mode, fs[k].flux_dir = s["instance"], s["mode"], s["flux_dir"]
@@ -339,6 +346,41 @@ def weno_cross_eval(h, instances, sets, fp64_check=False):
         fs[k].out = _ptr(s["out"], torch.float64 if fp64_check else torch.float32).value
     return _check(h, lib().weno_cross_eval(h, inst, len(instances), fs, len(sets),
                                            CROSS_FP64_CHECK if fp64_check else 0))
+
+
+class weno_tt_cross_problem(C.Structure):
+    _fields_ = [("r", C.c_int32 * 2), ("J1", C.c_void_p), ("J2", C.c_void_p), ("I1", C.c_void_p),
+                ("I2", C.c_void_p), ("core", C.c_void_p * 3)]
+
+
+def weno_tt_cross(h, instances, flux_dir, ranks, J1s, J2s, sweeps=1, delta=1e-2, fp64_check=False):
+    """TT-cross of the flux_dir residual of every instance.  ranks: [(r1, r2)];
+    J1s / J2s: initial right index sets, int32 CUDA tensors [r1][3] / [r2][2]
+    (updated in place).  Returns [dict(cores, I1, I2, J1, J2)] of CUDA tensors."""
+    import torch
+    inst = _instances(instances)
+    arr = (weno_tt_cross_problem * len(instances))()
+    outs = []
+    for i, d in enumerate(instances):
+        r1, r2 = ranks[i]
+        n = [int(x) for x in d["n"]]
+        o = dict(cores=[torch.empty((n[0], 1, r1), dtype=torch.float64, device="cuda"),
+                        torch.empty((n[1], r1, r2), dtype=torch.float64, device="cuda"),
+                        torch.empty((n[2], r2, 5), dtype=torch.float64, device="cuda")],
+                 I1=torch.empty(r1, dtype=torch.int32, device="cuda"),
+                 I2=torch.empty((r2, 2), dtype=torch.int32, device="cuda"), J1=J1s[i], J2=J2s[i])
+        P = arr[i]
+        P.r[0], P.r[1] = r1, r2
+        P.J1 = _ptr(J1s[i], torch.int32).value
+        P.J2 = _ptr(J2s[i], torch.int32).value
+        P.I1 = o["I1"].data_ptr()
+        P.I2 = o["I2"].data_ptr()
+        for m in range(3):
+            P.core[m] = o["cores"][m].data_ptr()
+        outs.append(o)
+    _check(h, lib().weno_tt_cross(h, inst, len(instances), int(flux_dir), arr, int(sweeps), float(delta),
+                                  CROSS_FP64_CHECK if fp64_check else 0))
+    return outs
 
 
 class Solver:

@@ -70,3 +70,86 @@ def test_maxvol_rejects_rank_deficient_matrices(W, H):
     with pytest.raises(W.WenoError) as e:
         W.weno_maxvol(H, [torch.from_numpy(A).cuda()])
     assert e.value.code == W.ERR_ARG
+
+
+# ------------------------------------------------------------ TT-cross driver
+import oracle as O  # noqa: E402
+from paper_2405_12301_gb300 import inputs as I  # noqa: E402
+
+
+def _instance(seed, n, r):
+    inst = I.tt_instance(seed=seed, n=n, r=r, device="cpu")
+    n, r, cores = inst["n"], inst["r"], inst["cores"]
+    U = np.stack([O.tt_full(n, r, cores[f]) for f in range(5)])
+    cfg = O.Cfg(dim=3, n=tuple(n), hi=(1.0, 1.0, 1.0), bc=((O.PERIODIC, O.PERIODIC),) * 3)
+    return dict(n=n, r=r, cores=cores, h=[1.0 / n[0], 1.0 / n[1], 1.0 / n[2]], bc=((0, 0),) * 3,
+                alpha=1.05 * O.alpha_max(cfg, U))
+
+
+def _dev(inst):
+    d = dict(inst)
+    d["cores"] = [[torch.from_numpy(c).cuda() for c in fc] for fc in inst["cores"]]
+    return d
+
+
+def _oracle_fun(inst, fd):
+    def fun(mode, left, right):
+        return O.cross_eval(inst["n"], inst["r"], inst["cores"], inst["h"], inst["alpha"], 1.4, 1e-6, inst["bc"],
+                            mode, fd, left, right)
+    return fun
+
+
+def _initial_sets(rng, n, r1, r2):
+    J1 = np.stack([rng.choice(n[1], r1), rng.choice(n[2], r1), rng.integers(0, 5, r1)], 1).astype(np.int32)
+    J2 = np.stack([rng.choice(n[2], r2, replace=False), rng.integers(0, 5, r2)], 1).astype(np.int32)
+    return J1, J2
+
+
+@pytest.mark.parametrize("fd,sweeps", [(0, 1), (1, 1), (2, 0), (2, 2)])
+def test_tt_cross_matches_oracle_fp64(W, H, fd, sweeps):
+    """Same function (the FP64 pointwise residual), same initial sets: the GPU
+    sweep selects the same index sets as the oracle and builds the same cores."""
+    rng = np.random.default_rng(10 + fd)
+    insts = [_instance(40 + k, [12, 16, 10], [3, 4]) for k in range(2)]
+    ranks = [(4, 6), (3, 5)]
+    sets = [_initial_sets(rng, insts[k]["n"], *ranks[k]) for k in range(2)]
+    outs = W.weno_tt_cross(H, [_dev(d) for d in insts], fd, ranks,
+                           [torch.from_numpy(s[0].copy()).cuda() for s in sets],
+                           [torch.from_numpy(s[1].copy()).cuda() for s in sets], sweeps=sweeps, fp64_check=True)
+    torch.cuda.synchronize()
+    for k in range(2):
+        G, I1, I2, J1, J2 = X.cross_sweeps(_oracle_fun(insts[k], fd), insts[k]["n"], ranks[k], sets[k][0], sets[k][1],
+                                           sweeps=sweeps)
+        o = outs[k]
+        assert o["I1"].cpu().numpy().tolist() == I1.tolist()
+        assert o["I2"].cpu().numpy().tolist() == I2.tolist()
+        assert o["J1"].cpu().numpy().tolist() == J1.tolist()
+        assert o["J2"].cpu().numpy().tolist() == J2.tolist()
+        T, To = X.tt4_full([c.cpu().numpy() for c in o["cores"]]), X.tt4_full(G)
+        assert np.abs(T - To).max() <= 1e-10 * np.abs(To).max()
+
+
+def test_tt_cross_fp32_interpolates_the_residual_on_its_sets(W, H):
+    """FP32 fiber evaluation: the TT equals the (FP64 oracle) residual on the
+    final cross to FP32 accuracy, and the first core is the identity on I1."""
+    rng = np.random.default_rng(20)
+    inst = _instance(50, [16, 12, 14], [4, 3])
+    r1, r2 = 5, 7
+    J1, J2 = _initial_sets(rng, inst["n"], r1, r2)
+    o, = W.weno_tt_cross(H, [_dev(inst)], 1, [(r1, r2)], [torch.from_numpy(J1).cuda()],
+                         [torch.from_numpy(J2).cuda()], sweeps=1)
+    torch.cuda.synchronize()
+    G = [c.cpu().numpy() for c in o["cores"]]
+    I1, I2, J2o = o["I1"].cpu().numpy(), o["I2"].cpu().numpy(), o["J2"].cpu().numpy()
+    assert np.allclose(G[0][I1, 0, :], np.eye(r1), atol=1e-12)
+    T = X.tt4_full(G)
+    fun = _oracle_fun(inst, 1)
+    A2 = fun(2, I2, np.zeros((1, 0), np.int32))           # A(I2, :, f)
+    scale = np.abs(A2).max()
+    for b in range(r2):
+        i, j = I2[b]
+        assert np.abs(T[i, j] - A2[:, b, :, 0].T).max() <= 1e-5 * scale
+    A1 = fun(1, I1[:, None].astype(np.int32), J2o[:, :1].astype(np.int32))   # A(I1, :, J2)
+    for b in range(r2):
+        k, f = J2o[b]
+        assert np.abs(T[I1][:, :, k, f] - A1[f, :, :, b]).max() <= 1e-5 * scale
