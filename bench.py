@@ -392,6 +392,46 @@ def bench_tt(weno, torch, insts, reps=5, eps=1e-6, dt=1e-3):
                          "flops": "Householder 2mk^2-2k^3/3 per QR, 4mkp-2k^2p per Q apply"}}
 
 
+def bench_tt_cross(weno, I, torch, insts, reps=3, fd=0, sweeps=1):
+    """The fixed-rank TT-cross of the x residual of all 64 instances in one
+    weno_tt_cross call (one right-to-left update between two left-to-right
+    passes), cross ranks equal to the instance ranks, seeded initial right
+    index sets, FP32 fiber evaluation and FP64 selection."""
+    import numpy as np
+    rng = np.random.default_rng(I.MASTER_SEED)
+    ranks, J1s, J2s = [], [], []
+    samples = 0
+    for d in insts:
+        n1, n2, n3 = d["n"]
+        r2 = min(d["r"][1], 5 * n3, 64)
+        r1 = min(d["r"][0], n1, n2 * r2, 64)
+        r2 = min(r2, r1 * n2)
+        ranks.append((r1, r2))
+        J1s.append(torch.from_numpy(np.stack([rng.integers(0, n2, r1), rng.integers(0, n3, r1),
+                                              rng.integers(0, 5, r1)], 1).astype(np.int32)).cuda())
+        J2s.append(torch.from_numpy(np.stack([rng.choice(n3, r2, replace=False), rng.integers(0, 5, r2)],
+                                             1).astype(np.int32)).cuda())
+        samples += (sweeps + 1) * (n1 * r1 + r1 * n2 * r2 + r2 * n3) + sweeps * r1 * n2 * r2
+    h = weno.weno_init(None)
+    weno.weno_tt_cross(h, insts, fd, ranks, J1s, J2s, sweeps=sweeps)
+    weno.weno_profile_enable(h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        weno.weno_tt_cross(h, insts, fd, ranks, J1s, J2s, sweeps=sweeps)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    kms, kn, launches = weno.weno_profile_read(h)
+    weno.weno_destroy(h)
+    return {"workload": "tt_cross_x_residual_64_instances", "value": samples / (ms * 1e-3) / 1e6,
+            "unit": "Msample/s", "ms_per_call": ms, "samples_per_call": samples, "sweeps": sweeps,
+            "kernels_ms_per_call": {"fiber_eval": kms[7] / reps, "qr": kms[0] / reps,
+                                    "maxvol_and_bookkeeping": kms[1] / reps},
+            "gpu_launches_per_call": launches / reps}
+
+
 def bench_cross(weno, I, torch, insts, reps=10):
     """The batched WENO-cross workload: the 64 TT instances, every sweep mode x
     flux direction (9 fiber sets per instance), all evaluated in one persistent
@@ -489,7 +529,7 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
-    ap.add_argument("--only", choices=["cross", "tt", "scalar"],
+    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--reps", type=int, default=5, help="timed calls of the --only measurement")
     args = ap.parse_args()
@@ -519,6 +559,8 @@ def main():
         insts = tt_workload(I, torch)
         if args.only == "cross":
             print(json.dumps(bench_cross(weno, I, torch, insts, reps=args.reps)))
+        elif args.only == "ttcross":
+            print(json.dumps(bench_tt_cross(weno, I, torch, insts, reps=args.reps)))
         else:
             print(json.dumps(bench_tt(weno, torch, insts, reps=args.reps)))
         return
@@ -563,6 +605,7 @@ def main():
     insts = tt_workload(I, torch) if (rank == 0 and not args.no_cross) else None
     cross = bench_cross(weno, I, torch, insts) if insts is not None else None
     ttr = bench_tt(weno, torch, insts) if insts is not None else None
+    ttx = bench_tt_cross(weno, I, torch, insts) if insts is not None else None
     acc = accuracy(weno, I, torch) if rank == 0 else None
     scalar = bench_scalar(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     rl = roofline(w, True, kms, kn, cells)
@@ -588,6 +631,7 @@ def main():
         "cross_eval": cross,
         "scalar_advection": scalar,
         "tt_round": ttr,
+        "tt_cross": ttx,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
