@@ -6,6 +6,7 @@
 // component, carried by the last core as in the LF-cross layout (Sec. 4.2).
 #include "weno_dev.cuh"
 #include "weno_internal.h"
+#include "tt_internal.h"
 
 namespace wg {
 

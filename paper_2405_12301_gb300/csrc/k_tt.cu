@@ -25,6 +25,7 @@
 
 #include "weno_dev.cuh"
 #include "weno_internal.h"
+#include "tt_internal.h"
 
 namespace wg {
 

@@ -12,6 +12,7 @@
 #include "../../include/weno_gb300.h"
 #include "weno_dev.cuh"
 #include "weno_internal.h"
+#include "tt_internal.h"
 
 using namespace wg;
 
