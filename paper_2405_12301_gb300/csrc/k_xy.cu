@@ -30,18 +30,27 @@ namespace xy {
 constexpr int NT = 256;
 constexpr int TX = 32, TY = 8;
 constexpr int BX = TX + 6, BY = TY + 6;     // row and column extents with halo
-constexpr int NXP = BX * TY;                // x-flux points: 38 x 8
+constexpr int BXP = BX + 3;                 // row pitch of the x-flux points (41: the sliding
+                                            // runs of phase W read 8 rows x 4 components per
+                                            // warp without bank conflicts)
+constexpr int NXP = BXP * TY;               // x-flux points: 38 (pitch 41) x 8
 constexpr int NYP = TX * BY;                // y-flux points: 32 x 14
 constexpr int NXI = (TX + 1) * TY;          // x interfaces: 33 x 8
 constexpr int NYI = TX * (TY + 1);          // y interfaces: 32 x 9
 constexpr int NHY = 6 * TX;                 // y-halo points (rows -3..-1, TY..TY+2)
 constexpr int NHALO = NHY + 6 * TY;         // plus x-halo points: 240
 
+// 2D grids reconstruct faces with sliding runs (one thread per line segment,
+// component and sign; WENO(+) and WENO(-) kept apart); 3D planes (five
+// components) one thread per cell.
+template <int D> constexpr bool slide() { return D == 2; }
+
 template <int D, bool BULK> struct Layout {
     using T = typename std::conditional<BULK, float, double>::type;
     static constexpr int NF = D + 2;
+    static constexpr int NS = slide<D>() ? 2 : 1;                             // face-flux copies
     static constexpr size_t F_off = 0;                                        // Fx, Fy
-    static constexpr size_t fx_off = (sizeof(T) * NF * (NXI + NYI) + 15) & ~size_t(15);
+    static constexpr size_t fx_off = (sizeof(T) * NS * NF * (NXI + NYI) + 15) & ~size_t(15);
     static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXP;
     static constexpr size_t ref_off = (fy_off + sizeof(T) * 2 * NF * NYP + 15) & ~size_t(15);
     static constexpr size_t bytes = ref_off + sizeof(RefState<D>);
@@ -56,9 +65,9 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     using T = typename L::T;
     constexpr int NF = L::NF;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *Fx = reinterpret_cast<T *>(smem + L::F_off);        // [NF][TY][TX+1]
-    T *Fy = Fx + NF * NXI;                                 // [NF][TY+1][TX]
-    T *fx = reinterpret_cast<T *>(smem + L::fx_off);       // [2][NF][TY][BX]
+    T *Fx = reinterpret_cast<T *>(smem + L::F_off);        // [NS][NF][TY][TX+1]
+    T *Fy = Fx + L::NS * NF * NXI;                         // [NS][NF][TY+1][TX]
+    T *fx = reinterpret_cast<T *>(smem + L::fx_off);       // [2][NF][TY][BXP]
     T *fy = reinterpret_cast<T *>(smem + L::fy_off);       // [2][NF][BY][TX]
     RefState<D> &ref = *reinterpret_cast<RefState<D> *>(smem + L::ref_off);
 
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
             else split_flux_f64<D, 1>(q, alY, gm1, fp, fm);
         }
         if (dirx) {
-            const int o = ly * BX + (lx + 3);
+            const int o = ly * BXP + (lx + 3);
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 fx[f * NXP + o] = fp[f];
@@ -206,8 +215,8 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     // one of the remaining faces (top of the tile's top row, right of its last column)
     const T eps = BULK ? (T)a.eps_f : (T)a.eps;
     auto face_x = [&](int f, int ly, int j) -> T {  // between local columns j-1 and j of row ly
-        const T *P = fx + f * NXP + ly * BX;
-        const T *M = fx + (NF + f) * NXP + ly * BX;
+        const T *P = fx + f * NXP + ly * BXP;
+        const T *M = fx + (NF + f) * NXP + ly * BXP;
         return weno5<T>(P[j], P[j + 1], P[j + 2], P[j + 3], P[j + 4], eps) +
                weno5<T>(M[j + 5], M[j + 4], M[j + 3], M[j + 2], M[j + 1], eps);
     };
@@ -218,22 +227,58 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
     };
     T fxl[NF], fyb[NF];
+    if constexpr (slide<D>()) {
+        // Two runs of TY + 1 = 9 windows per thread, one code path (a single
+        // unrolled copy keeps the kernel inside the instruction cache):
+        //   y: column `lane`, component w & 3, sign w >> 2, faces 0..8;
+        //   x: row lane & 7, component lane >> 3, sign w >> 2, faces 8 s .. 8 s + 8
+        //      for s = w & 3 -- neighbouring segments share one face and write it
+        //      with the same value (each window is formed from its own five points).
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, sg = w >> 2;
+#pragma unroll 1
+        for (int item = 0; item < 2; ++item) {
+            const T *p;
+            T *out;
+            int st, os;
+            if (item == 0) {
+                const int f = w & 3;
+                p = fy + (sg * NF + f) * NYP + lane;
+                out = Fy + (sg * NF + f) * NYI + lane;
+                st = TX;
+                os = TX;
+            } else {
+                const int ly = lane & 7, f = lane >> 3, j0 = (w & 3) * 8;
+                p = fx + (sg * NF + f) * NXP + ly * BXP + j0;
+                out = Fx + (sg * NF + f) * NXI + ly * (TX + 1) + j0;
+                st = 1;
+                os = 1;
+            }
+            if (sg) {  // WENO(-): the same run read backwards from the far end
+                p += (TY + 5) * st;
+                out += TY * os;
+                st = -st;
+                os = -os;
+            }
+            weno5_slide<T, TY + 1>(p, st, eps, out, os);
+        }
+    } else {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        fxl[f] = face_x(f, ty, tx);
-        Fx[f * NXI + ty * (TX + 1) + tx] = fxl[f];
-        fyb[f] = face_y(f, tx, ty);
-        Fy[f * NYI + ty * TX + tx] = fyb[f];
-    }
-    if (threadIdx.x < NF * (TX + TY)) {
-        const int t = threadIdx.x;
-        if (t < NF * TX) {
-            const int f = t >> 5, lx = t & 31;
-            Fy[f * NYI + TY * TX + lx] = face_y(f, lx, TY);
-        } else {
-            const int u = t - NF * TX;
-            const int f = u >> 3, ly = u & 7;
-            Fx[f * NXI + ly * (TX + 1) + TX] = face_x(f, ly, TX);
+        for (int f = 0; f < NF; ++f) {
+            fxl[f] = face_x(f, ty, tx);
+            Fx[f * NXI + ty * (TX + 1) + tx] = fxl[f];
+            fyb[f] = face_y(f, tx, ty);
+            Fy[f * NYI + ty * TX + tx] = fyb[f];
+        }
+        if (threadIdx.x < NF * (TX + TY)) {
+            const int t = threadIdx.x;
+            if (t < NF * TX) {
+                const int f = t >> 5, lx = t & 31;
+                Fy[f * NYI + TY * TX + lx] = face_y(f, lx, TY);
+            } else {
+                const int u = t - NF * TX;
+                const int f = u >> 3, ly = u & 7;
+                Fx[f * NXI + ly * (TX + 1) + TX] = face_x(f, ly, TX);
+            }
         }
     }
     __syncthreads();
@@ -244,8 +289,16 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     T r[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        const T dx = Fx[f * NXI + ty * (TX + 1) + tx + 1] - fxl[f];
-        const T dy = Fy[f * NYI + (ty + 1) * TX + tx] - fyb[f];
+        T dx, dy;
+        if constexpr (slide<D>()) {  // F^ = WENO(+) + WENO(-) at the right/top and left/bottom faces
+            const int ox = f * NXI + ty * (TX + 1) + tx, oy = f * NYI + ty * TX + tx;
+            const T *FxM = Fx + NF * NXI, *FyM = Fy + NF * NYI;
+            dx = (Fx[ox + 1] + FxM[ox + 1]) - (Fx[ox] + FxM[ox]);
+            dy = (Fy[oy + TX] + FyM[oy + TX]) - (Fy[oy] + FyM[oy]);
+        } else {
+            dx = Fx[f * NXI + ty * (TX + 1) + tx + 1] - fxl[f];
+            dy = Fy[f * NYI + (ty + 1) * TX + tx] - fyb[f];
+        }
         r[f] = -dx * ihx - dy * ihy;
     }
     if (EPI == EPI_STORE) {

@@ -167,6 +167,54 @@ __device__ __forceinline__ T weno5(T a, T b, T c, T d, T e, T eps)
     return c + div_<T>(num, T(6) * sw);
 }
 
+// WENO5 of K consecutive windows along a line, sharing what neighbouring
+// windows have in common: window m is (p[m s], ..., p[(m + 4) s]) and its value
+// goes to out[m os].  Moving to the next window drops the first point, so its
+// first differences D1..D3, second differences t1, t2 and the 13/12 t^2 parts
+// of beta_1, beta_2 are the previous window's D2..D4, t0, t1 and beta_0, beta_1
+// parts; each window loads one new point and forms one new difference of each
+// kind.  Every window's value is formed from its five points by the same
+// operations wherever it sits in the run (the first window forms its shared
+// terms directly from the same differences), so a face computed by two runs
+// gets bitwise the same value.  A negative stride s walks a line backwards,
+// which turns the run into the mirrored WENO(-) of the faces in reverse order.
+template <typename T, int K>
+__device__ __forceinline__ void weno5_slide(const T *p, int s, T eps, T *out, int os)
+{
+    const T k13 = T(13.0 / 12.0), q = T(0.25);
+    const T v0 = *p, v1 = *(p += s);
+    T c = *(p += s), d = *(p += s);
+    T D1 = v1 - v0, D2 = c - v1, D3 = d - c;
+    T t1 = D3 - D2, t2 = D2 - D1;
+    T A1 = fma(k13 * t1, t1, eps), A2 = fma(k13 * t2, t2, eps);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        const T e = *(p += s);
+        const T D4 = e - d;
+        const T t0 = D4 - D3;
+        const T A0 = fma(k13 * t0, t0, eps);
+        const T s0 = fma(T(-3), D3, D4), s1 = D2 + D3, s2 = fma(T(3), D2, -D1);
+        T g0 = fma(q * s0, s0, A0), g1 = fma(q * s1, s1, A1), g2 = fma(q * s2, s2, A2);
+        g0 *= g0;
+        g1 *= g1;
+        g2 *= g2;
+        const T w0 = T(0.3) * (g1 * g2), w1 = T(0.6) * (g0 * g2), w2 = T(0.1) * (g0 * g1);
+        const T sw = w0 + w1 + w2;
+        const T num = fma(w0, t1 - t0, fma(T(-2) * w2, t1 - t2, fma(T(2), D3, D2) * sw));
+        *out = c + div_<T>(num, T(6) * sw);
+        out += os;
+        D1 = D2;
+        D2 = D3;
+        D3 = D4;
+        t2 = t1;
+        t1 = t0;
+        A2 = A1;
+        A1 = A0;
+        c = d;
+        d = e;
+    }
+}
+
 // ----------------------------------------------------------- point fluxes
 
 // Plain FP64 Euler flux in direction DIR (Sec. 2.1) and its LF split
