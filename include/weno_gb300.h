@@ -256,7 +256,14 @@ typedef struct {
     void *out;
 } weno_fiber_set;
 
-enum { WENO_CROSS_FP64_CHECK = 1 };
+/* WENO_CROSS_FP64_CHECK: evaluate in FP64 and write FP64 outputs.
+ * WENO_CROSS_GRAPH: run the evaluation as a CUDA graph captured for these
+ * exact descriptors (instance and fiber-set fields, pointers included) and
+ * replay it on later calls with the same descriptors -- the device arrays they
+ * point to (index sets, cores, outputs) may hold new contents.  The handle
+ * keeps up to 16 such graphs, each with its own scratch; the first call of a
+ * descriptor set synchronises the stream once. */
+enum { WENO_CROSS_FP64_CHECK = 1, WENO_CROSS_GRAPH = 2 };
 
 /* Evaluates every fiber set on the handle's stream: one launch contracts the
  * left and right TT vectors of every set, one persistent launch evaluates all
@@ -269,6 +276,26 @@ enum { WENO_CROSS_FP64_CHECK = 1 };
  * the next synchronising call returns WENO_ERR_ARG. */
 int weno_cross_eval(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, const weno_fiber_set *sets,
                     int32_t n_sets, int32_t flags);
+
+/* Autotuner of the evaluation kernel: times every compiled variant of it
+ * (threads per CTA x samples per shared-memory chunk) with every persistent
+ * grid of 1..4 CTAs per SM on this workload, reps timed runs each after a
+ * warm-up (the outputs are written), and keeps the fastest for the workload's
+ * class (precision, rank bucket 8/16/32, samples per call to a factor of 4);
+ * later weno_cross_eval calls of that class use it.  choice (host int[3], may
+ * be NULL): threads per CTA, samples per chunk, CTAs per SM; ms (host, may be
+ * NULL): its time per evaluation.  Synchronises.  Errors: those of
+ * weno_cross_eval, WENO_ERR_ARG for reps < 1. */
+int weno_cross_autotune(weno_handle h, const weno_tt_instance *inst, int32_t n_inst, const weno_fiber_set *sets,
+                        int32_t n_sets, int32_t flags, int32_t reps, int32_t *choice, double *ms);
+
+/* Tuning cache file.  weno_tune_save writes the handle's choices (a first line
+ * naming the GPU model and SM count, then one line per workload class);
+ * weno_tune_load reads a file written on the same GPU model (a file from
+ * another model loads nothing) and reports the entries taken in *n_loaded.
+ * Errors: WENO_ERR_ARG for a null path or a file that cannot be opened. */
+int weno_tune_save(weno_handle h, const char *path);
+int weno_tune_load(weno_handle h, const char *path, int32_t *n_loaded);
 
 /* ------------------------------------------------------------------------
  * TT-rounding (Sec. 3, "TT-rounding": Oseledets' two-pass algorithm) of sums

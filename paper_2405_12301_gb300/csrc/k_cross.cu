@@ -24,14 +24,21 @@
 // Ghost rows (Sec. 4.5) are mapped by the boundary rule of fd.
 #include "weno_dev.cuh"
 #include "weno_internal.h"
+#include "cross_internal.h"
 
 namespace wg {
 
-constexpr int XT = 256;       // threads per CTA
+constexpr int XT = 256;       // threads per CTA of k_cross_vecs
 constexpr int VP = 32;        // padded vector length (largest rank)
 constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 consecutive rows hit distinct banks
-constexpr int CH = 64;        // samples per chunk
-constexpr int CP = CH + 6;    // chunk points including the stencil halo
+// k_cross is compiled for several (threads per CTA, samples per chunk) pairs;
+// the autotuner of weno_api.cu picks one, and the persistent grid size, per
+// workload class.  Variant 0 is the default.
+// minb > 1 asks the compiler for registers that fit minb CTAs per SM.
+struct CrossVariant { int threads, chunk, minb; };
+constexpr CrossVariant kCrossVariants[] = {{256, 64, 1}, {256, 32, 1}, {128, 64, 1}, {128, 32, 1},
+                                           {256, 128, 1}, {256, 64, 3}, {128, 64, 6}};
+constexpr int kNumCrossVariants = sizeof(kCrossVariants) / sizeof(kCrossVariants[0]);
 
 template <typename T> __device__ __forceinline__ T cvtf(float x) { return (T)x; }
 
@@ -143,10 +150,11 @@ __global__ void __launch_bounds__(XT) k_cross_vecs(const CrossArgs A)
 }
 
 // ------------------------------------------------------------------- main
-template <bool F64>
-__global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
+template <bool F64, int XT, int CH, int MINB>
+__global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
 {
     using T = typename std::conditional<F64, double, float>::type;
+    constexpr int CP = CH + 6;  // chunk points including the stencil halo
     extern __shared__ __align__(16) unsigned char dyn[];
     T *C = reinterpret_cast<T *>(dyn);        // [5][CP][CS] contracted core rows of the chunk
     T *Cref = C + 5 * CP * CS;                // [5][CS]     chunk reference row (FP32, fd == mode)
@@ -357,35 +365,71 @@ __global__ void __launch_bounds__(XT) k_cross(const CrossArgs A)
     }
 }
 
-static size_t cross_dyn_bytes(bool f64)
+static size_t cross_dyn_bytes(bool f64, int chunk)
 {
     const size_t e = f64 ? sizeof(double) : sizeof(float);
-    return e * (size_t)(5 * CP * CS + 2 * 5 * CS);
+    return e * (size_t)(5 * (chunk + 6) * CS + 2 * 5 * CS);
 }
 
 int cross_vec_len() { return VP; }
-
-cudaError_t launch_cross(const CrossArgs &a, cudaStream_t s)
+int cross_num_variants() { return kNumCrossVariants; }
+void cross_variant(int v, int *threads, int *chunk)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_cross<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)cross_dyn_bytes(false));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_cross<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)cross_dyn_bytes(true));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    *threads = kCrossVariants[v].threads;
+    *chunk = kCrossVariants[v].chunk;
+}
+
+template <bool F64, int V>
+static cudaError_t set_attr()
+{
+    constexpr int XT_ = kCrossVariants[V].threads, CH_ = kCrossVariants[V].chunk, MB_ = kCrossVariants[V].minb;
+    return cudaFuncSetAttribute(k_cross<F64, XT_, CH_, MB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cross_dyn_bytes(F64, CH_));
+}
+
+// Shared-memory limits of every variant, set once before any launch (and so
+// never inside a stream capture).
+cudaError_t cross_set_attributes()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaSuccess, r;
+#define X(V) \
+    if ((r = set_attr<false, V>()) != cudaSuccess) e = r; \
+    if ((r = set_attr<true, V>()) != cudaSuccess) e = r;
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6)
+#undef X
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <bool F64, int V>
+static cudaError_t launch_main(const CrossArgs &a, long long blocks, cudaStream_t s)
+{
+    constexpr int XT_ = kCrossVariants[V].threads, CH_ = kCrossVariants[V].chunk, MB_ = kCrossVariants[V].minb;
+    k_cross<F64, XT_, CH_, MB_><<<(unsigned)blocks, XT_, cross_dyn_bytes(F64, CH_), s>>>(a);
+    return cudaGetLastError();
+}
+
+// variant: index into kCrossVariants; ctas_per_sm: persistent grid = 152 x that
+// (capped by the number of work items).
+cudaError_t launch_cross(const CrossArgs &a, int variant, int ctas_per_sm, cudaStream_t s)
+{
+    if (variant < 0 || variant >= kNumCrossVariants || ctas_per_sm < 1) return cudaErrorInvalidValue;
+    cudaError_t ea = cross_set_attributes();
+    if (ea != cudaSuccess) return ea;
     if (a.fp64) k_cross_vecs<true><<<a.n_sets, XT, 0, s>>>(a);
     else k_cross_vecs<false><<<a.n_sets, XT, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    long long blocks = a.n_work < 152 * 4 ? a.n_work : 152 * 4;
+    long long blocks = 152LL * ctas_per_sm;
+    if (blocks > a.n_work) blocks = a.n_work;
     if (blocks < 1) blocks = 1;
-    if (a.fp64) k_cross<true><<<(unsigned)blocks, XT, cross_dyn_bytes(true), s>>>(a);
-    else k_cross<false><<<(unsigned)blocks, XT, cross_dyn_bytes(false), s>>>(a);
-    return cudaGetLastError();
+#define X(V)                                                                             \
+    if (variant == V) return a.fp64 ? launch_main<true, V>(a, blocks, s) : launch_main<false, V>(a, blocks, s);
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
 int cross_max_rank() { return VP; }

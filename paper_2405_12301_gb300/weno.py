@@ -17,12 +17,13 @@ BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 FP64, FP32_BULK = 0, 1
 ALPHA_GLOBAL_NORM, ALPHA_PER_DIR = 0, 1
 MODEL_EULER, MODEL_ADVECT, MODEL_BURGERS = 0, 1, 2
-CROSS_FP64_CHECK = 1
+CROSS_FP64_CHECK, CROSS_GRAPH = 1, 2
 
 EXPORTS = ("weno_init", "weno_destroy", "weno_set_stream", "weno_alpha", "weno_rhs", "weno_set_time",
            "weno_get_time", "weno_ssprk3_step", "weno_run", "weno_run_host", "weno_sums", "weno_sync",
            "weno_last_error", "weno_cross_eval", "weno_profile_enable", "weno_profile_read",
-           "weno_sums_noalloc", "weno_tt_round", "weno_maxvol", "weno_tt_cross")
+           "weno_sums_noalloc", "weno_tt_round", "weno_maxvol", "weno_tt_cross", "weno_cross_autotune",
+           "weno_tune_save", "weno_tune_load")
 PROFILE_KINDS = 8
 
 
@@ -103,6 +104,10 @@ def lib():
         L.weno_tt_round.argtypes = [vp, P(weno_tt_round_problem), i32, d]
         L.weno_maxvol.argtypes = [vp, P(weno_maxvol_problem), i32, d, i32, P(i32)]
         L.weno_tt_cross.argtypes = [vp, P(weno_tt_instance), i32, i32, P(weno_tt_cross_problem), i32, d, i32]
+        L.weno_cross_autotune.argtypes = [vp, P(weno_tt_instance), i32, P(weno_fiber_set), i32, i32, i32, P(i32),
+                                          P(d)]
+        L.weno_tune_save.argtypes = [vp, C.c_char_p]
+        L.weno_tune_load.argtypes = [vp, C.c_char_p, P(i32)]
         for name in EXPORTS:
             if name != "weno_last_error":
                 getattr(L, name).restype = C.c_int
@@ -331,11 +336,8 @@ def _instances(instances):
     return inst
 
 
-def weno_cross_eval(h, instances, sets, fp64_check=False):
-    """instances: list of dict(n, r, cores=[5][3] CUDA float32 tensors, h, alpha, bc);
-    sets: list of dict(instance, mode, flux_dir, left, right, out) with CUDA tensors."""
+def _fiber_sets(sets, fp64_check):
     import torch
-    inst = _instances(instances)
     fs = (weno_fiber_set * len(sets))()
     for k, s in enumerate(sets):
         fs[k].instance, fs[k].mode, fs[k].flux_dir = s["instance"], s["mode"], s["flux_dir"]
@@ -344,8 +346,38 @@ def weno_cross_eval(h, instances, sets, fp64_check=False):
         fs[k].left = _ptr(s["left"], torch.int32).value if s["left"] is not None else None
         fs[k].right = _ptr(s["right"], torch.int32).value if s["right"] is not None else None
         fs[k].out = _ptr(s["out"], torch.float64 if fp64_check else torch.float32).value
-    return _check(h, lib().weno_cross_eval(h, inst, len(instances), fs, len(sets),
-                                           CROSS_FP64_CHECK if fp64_check else 0))
+    return fs
+
+
+def weno_cross_eval(h, instances, sets, fp64_check=False, graph=False):
+    """instances: list of dict(n, r, cores=[5][3] CUDA float32 tensors, h, alpha, bc);
+    sets: list of dict(instance, mode, flux_dir, left, right, out) with CUDA tensors."""
+    inst = _instances(instances)
+    fs = _fiber_sets(sets, fp64_check)
+    flags = (CROSS_FP64_CHECK if fp64_check else 0) | (CROSS_GRAPH if graph else 0)
+    return _check(h, lib().weno_cross_eval(h, inst, len(instances), fs, len(sets), flags))
+
+
+def weno_cross_autotune(h, instances, sets, fp64_check=False, reps=3):
+    """Times every kernel variant and grid size on this workload; returns
+    ((threads per CTA, samples per chunk, CTAs per SM), ms per evaluation)."""
+    inst = _instances(instances)
+    fs = _fiber_sets(sets, fp64_check)
+    choice = (C.c_int32 * 3)()
+    ms = C.c_double()
+    _check(h, lib().weno_cross_autotune(h, inst, len(instances), fs, len(sets), CROSS_FP64_CHECK if fp64_check else 0,
+                                        int(reps), choice, C.byref(ms)))
+    return tuple(choice), ms.value
+
+
+def weno_tune_save(h, path):
+    return _check(h, lib().weno_tune_save(h, os.fsencode(path)))
+
+
+def weno_tune_load(h, path):
+    n = C.c_int32()
+    _check(h, lib().weno_tune_load(h, os.fsencode(path), C.byref(n)))
+    return n.value
 
 
 class weno_tt_cross_problem(C.Structure):

@@ -198,3 +198,76 @@ def test_cross_eval_full_workload_sampled(W):
         assert np.isfinite(got).all()
         assert (np.abs(got - ref) <= 2e-3 * scale + 1e-3).all(), (k, mode, fd, float(np.abs(got - ref).max()))
     W.weno_destroy(h)
+
+
+def _uneven_workload():
+    insts = [make_instance(31, [24, 40, 18], [5, 7], (O.PERIODIC,) * 2),
+             make_instance(32, [36, 20, 30], [9, 4], (O.REFLECTIVE,) * 2)]
+    allsets, allrefs = [], []
+    for k, inst in enumerate(insts):
+        for fp64 in (True,):
+            sets, refs = make_sets(inst, k, 120 + k, fp64)
+            allsets += sets
+            allrefs += [(k,) + r for r in refs]
+    return insts, allsets, allrefs
+
+
+def test_cross_graph_replays_with_new_index_contents(W):
+    """WENO_CROSS_GRAPH: the first call captures, later calls with the same
+    descriptors replay; the index arrays are changed in place between calls and
+    every replay equals a direct evaluation of the same inputs (bitwise: same
+    kernels, same configuration)."""
+    insts, sets, refs = _uneven_workload()
+    dinsts = [dev_instance(i) for i in insts]
+    h = W.weno_init(None)
+    rng = np.random.default_rng(8)
+    for rep in range(3):
+        if rep:
+            for s, (k, mode, fd, left, right) in zip(sets, refs):
+                n = insts[k]["n"]
+                if s["left"] is not None:
+                    s["left"].copy_(torch.from_numpy(np.stack([rng.integers(0, n[m], s["left"].shape[0])
+                                                               for m in range(mode)], 1).astype(np.int32)))
+                if s["right"] is not None:
+                    s["right"].copy_(torch.from_numpy(np.stack([rng.integers(0, n[m], s["right"].shape[0])
+                                                                for m in range(mode + 1, 3)], 1).astype(np.int32)))
+        W.weno_cross_eval(h, dinsts, sets, fp64_check=True, graph=True)
+        W.weno_sync(h)
+        got = [s["out"].clone() for s in sets]
+        W.weno_cross_eval(h, dinsts, sets, fp64_check=True)
+        W.weno_sync(h)
+        for g, s in zip(got, sets):
+            assert torch.equal(g, s["out"])
+        # and the values are the oracle's
+        k, mode, fd, _, _ = refs[4]
+        left = sets[4]["left"].cpu().numpy() if sets[4]["left"] is not None else np.zeros((1, 0), np.int32)
+        right = sets[4]["right"].cpu().numpy() if sets[4]["right"] is not None else np.zeros((1, 0), np.int32)
+        ref = oracle_out(insts[k], mode, fd, left, right)
+        assert (np.abs(got[4].cpu().numpy() - ref) <= tol_fp64(ref, insts[k])).all()
+    W.weno_destroy(h)
+
+
+def test_autotune_picks_a_compiled_variant_and_keeps_results(W, tmp_path):
+    """The tuner times every variant; FP64 evaluation with the tuned variant is
+    bitwise the default one's (the per-sample arithmetic does not depend on the
+    chunking), and the choice survives a save / load through the cache file."""
+    insts, sets, refs = _uneven_workload()
+    dinsts = [dev_instance(i) for i in insts]
+    h0 = W.weno_init(None)
+    W.weno_cross_eval(h0, dinsts, sets, fp64_check=True)
+    W.weno_sync(h0)
+    base = [s["out"].clone() for s in sets]
+    h = W.weno_init(None)
+    choice, ms = W.weno_cross_autotune(h, dinsts, sets, fp64_check=True, reps=1)
+    print("tuned:", choice, "%.3f ms" % ms)
+    assert choice[0] in (128, 256) and choice[1] in (32, 64, 128) and 1 <= choice[2] <= 4 and ms > 0
+    W.weno_cross_eval(h, dinsts, sets, fp64_check=True)
+    W.weno_sync(h)
+    for b, s in zip(base, sets):
+        assert torch.equal(b, s["out"])
+    path = str(tmp_path / "tune.txt")
+    W.weno_tune_save(h, path)
+    h2 = W.weno_init(None)
+    assert W.weno_tune_load(h2, path) >= 1
+    for x in (h0, h, h2):
+        W.weno_destroy(x)
