@@ -4,7 +4,7 @@ kernel, the L1 error reached, an end-to-end number through host buffers, and
 the oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload 2d|3d]
+                  [--workload 2d|3d|3d384]
 
 A step is one SSP-RK3 step (three stages, each a full residual over the grid
 plus the stage combination) of the 2D periodic density wave on 2048^2
@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "2d": dict(dim=2, n=(2048, 2048), name="2d_density_wave_2048sq"),
     "3d": dict(dim=3, n=(256, 256, 256), name="3d_density_wave_256cube"),
+    "3d384": dict(dim=3, n=(384, 384, 384), name="3d_density_wave_384cube"),
 }
 
 # Algorithmic FP64/FP32 operation counts of the scheme as the paper writes it

@@ -143,3 +143,16 @@ def test_3d_wave_to_half_time(W):
     l1 = np.abs(u32[0] - ex).mean()
     print("3D 256^3 FP32-bulk to t=0.5: %d steps, L1(rho) = %.3e" % (st, l1))
     assert l1 < 1e-6
+
+
+def test_3d_384_cube_run_to_half_time(W):
+    """Config 4 at 384^3: FP32-bulk, CUDA-graph-captured steps to t = 0.5; the L1
+    error of rho against the exact wave is the scheme's (below the 256^3 run's)."""
+    N = 384
+    n = (N, N, N)
+    cfg = O.Cfg(dim=3, n=n, lo=(0, 0, 0), hi=(2.0, 2.0, 2.0))
+    u32, st = gpu_run(W, cfg, I.density_wave(3, n), 0.5, W.FP32_BULK)
+    ex = I.density_wave(3, n, t=0.5)[0]
+    l1 = np.abs(u32[0] - ex).mean()
+    print("3D 384^3 FP32-bulk to t=0.5: %d steps, L1(rho) = %.3e" % (st, l1))
+    assert l1 < 1e-6

@@ -470,3 +470,36 @@ def test_inflow_fp64_matches_oracle(W, dim, n, bc):
     sb.rhs(dev(U), Rd)
     used = [st[k][side][:nf] for k in range(dim) for side in range(2) if bc[k][side] == IN]
     assert (np.abs(host(Rd) - Rref) <= _variation_tol(cfg, U, Rref, aref[0], used)).all()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_384_cube_z_only_field_matches_1d_oracle(W, precision):
+    """384^3 (the larger 3D grid, a 2.26 GB state): a state varying along z only
+    has zero x and y flux differences, so every z-line of the residual -- formed
+    by the z kernel after the x+y kernel -- equals the 1D oracle residual of that
+    line (with the 3D alpha)."""
+    N = 384
+    cfg3 = O.Cfg(dim=3, n=(N, N, N), lo=(0, 0, 0), hi=(2.0, 2.0, 2.0))
+    U1 = I.random_state(1, (N,), seed=23, jumps=True, length=2.0)  # rho, rho w, E along z
+    z = lambda a: np.ascontiguousarray(np.broadcast_to(a[:, None, None], (N, N, N)))
+    U3 = np.zeros((5, N, N, N))
+    U3[0] = z(U1[0, 0, 0])
+    U3[3] = z(U1[1, 0, 0])
+    U3[4] = z(U1[2, 0, 0])
+    s = solver(W, cfg3, precision=precision)
+    Ud = dev(U3)
+    del U3
+    Rd = torch.empty(Ud.shape, dtype=torch.float64, device="cuda")
+    ad = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s.rhs(Ud, Rd, ad)
+    alpha = float(host(ad)[0])
+    cfg1 = O.Cfg(dim=1, n=(N,), lo=(0.0,), hi=(2.0,))
+    R1 = O.residual_dirs(cfg1, U1, alpha)
+    Rg = Rd.cpu().numpy()
+    tol1 = fp64_rhs_tol(cfg1, U1, R1, alpha) if precision == 0 else _variation_tol(cfg1, U1, R1, alpha)
+    for f, f1 in ((0, 0), (3, 1), (4, 2)):
+        want = R1[f1, 0, 0][:, None, None]
+        err = np.abs(Rg[f] - want) - tol1[f1, 0, 0][:, None, None]
+        assert err.max() <= 0.0, (f, float(err.max()))
+    for f in (1, 2):
+        assert np.abs(Rg[f]).max() <= 1e-12 * max(1.0, np.abs(R1).max())
