@@ -156,3 +156,28 @@ def test_3d_384_cube_run_to_half_time(W):
     l1 = np.abs(u32[0] - ex).mean()
     print("3D 384^3 FP32-bulk to t=0.5: %d steps, L1(rho) = %.3e" % (st, l1))
     assert l1 < 1e-6
+
+
+def test_2d_quadrant_1024_and_2048_runs(W):
+    """Config 3 at its own sizes: 1024^2 in FP64 and FP32-bulk and 2048^2 in
+    FP32-bulk, transmissive, to t = 0.3.  FP32-bulk stays within a bounded
+    distance of FP64 (the 256^2 bound), the states stay physical, and the
+    mass sums change only by the boundary fluxes (bounded by the run length)."""
+    T = O.TRANSMISSIVE
+    for N in (1024, 2048):
+        n = (N, N)
+        cfg = O.Cfg(dim=2, n=n, bc=((T, T), (T, T)))
+        U0 = I.quadrant_riemann(n)
+        m0 = O.sums(cfg, U0)
+        u32, st32 = gpu_run(W, cfg, U0, 0.3, W.FP32_BULK)
+        assert np.isfinite(u32).all() and u32[0].min() > 0
+        m32 = O.sums(cfg, u32)
+        line = "quadrant %d^2: %d steps FP32-bulk; mass %.6f -> %.6f" % (N, st32, m0[0], m32[0])
+        if N == 1024:
+            u64, st64 = gpu_run(W, cfg, U0, 0.3, W.FP64)
+            d = np.abs(u32[0] - u64[0]).mean() / np.abs(u64[0]).mean()
+            line += "; FP64 %d steps, FP32-bulk vs FP64 L1(rho)/mean = %.2e" % (st64, d)
+            assert d < 1e-4
+        print(line)
+        # the corner states move outwards at most ~1.5 (speeds < |u| + a): mass leaves only near the edges
+        assert abs(m32[0] - m0[0]) < 0.1 * m0[0]
