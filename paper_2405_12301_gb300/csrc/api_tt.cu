@@ -398,8 +398,8 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
     int max_r = 1;
     for (int i = 0; i < n_probs; ++i) {
         const weno_maxvol_problem &P = probs[i];
-        if (P.r < 1 || P.r > MV_RMAX || P.n < P.r || !P.A || !P.B || !P.idx)
-            return fail(h, WENO_ERR_ARG, "weno_maxvol: need 1 <= r <= 64, n >= r and non-null A, B, idx");
+        if (P.r < 1 || P.r > MV_RMAX || P.n < P.r || P.n > MV_NMAX || !P.A || !P.B || !P.idx)
+            return fail(h, WENO_ERR_ARG, "weno_maxvol: need 1 <= r <= 64, r <= n <= 65536 and non-null A, B, idx");
         w_total += (((size_t)P.n * P.r + 31) & ~size_t(31));
         max_r = std::max(max_r, (int)P.r);
     }

@@ -20,31 +20,37 @@ namespace wg {
 
 constexpr int MV_NT = 256, MV_NW = MV_NT / 32;
 
-// Block-wide argmax of (v, i): largest v, smallest i among equal v.  Every
-// thread gets the winner.  v must be >= 0 or -1 (excluded).
-__device__ __forceinline__ void block_argmax(double &v, long long &i, double *sv, long long *si)
+// |x| as an unsigned integer: for finite x its order is the order of |x|, so
+// argmaxes run on the integer pipe (FP64 compares issue at the FP64 rate).
+__device__ __forceinline__ unsigned long long absbits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Block-wide argmax of (key, i): largest key, smallest i among equal keys.
+__device__ __forceinline__ void block_argmax_u(unsigned long long &k, long long &i, unsigned long long *sk, long long *si)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const unsigned long long ok = __shfl_xor_sync(0xFFFFFFFFu, k, o);
         const long long oi = __shfl_xor_sync(0xFFFFFFFFu, i, o);
-        if (ov > v || (ov == v && oi < i)) {
-            v = ov;
+        if (ok > k || (ok == k && oi < i)) {
+            k = ok;
             i = oi;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();  // earlier readers of sv/si are done
+    __syncthreads();
     if (lane == 0) {
-        sv[warp] = v;
+        sk[warp] = k;
         si[warp] = i;
     }
     __syncthreads();
-    v = sv[0];
+    k = sk[0];
     i = si[0];
     for (int w = 1; w < MV_NW; ++w)
-        if (sv[w] > v || (sv[w] == v && si[w] < i)) {
-            v = sv[w];
+        if (sk[w] > k || (sk[w] == k && si[w] < i)) {
+            k = sk[w];
             i = si[w];
         }
 }
@@ -59,41 +65,44 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, doubl
     double *G = sm;                                  // [r][2r]: [A[I] | identity] for Gauss-Jordan
     double *row = G + (size_t)r * 2 * r;             // [r]
     int *I = reinterpret_cast<int *>(row + r);       // [r]
-    __shared__ double sv[MV_NW];
+    __shared__ unsigned long long sk[MV_NW];
     __shared__ long long si[MV_NW];
     __shared__ int s_fail;
+    __shared__ unsigned chosen[MV_NMAX / 32];  // rows already picked by the pivoting
     double *W = d.W, *B = d.B;
     const long long nr = (long long)n * r;
     if (threadIdx.x == 0) s_fail = 0;
+    for (int e = threadIdx.x; e < (n + 31) / 32; e += MV_NT) chosen[e] = 0u;
     for (long long e = threadIdx.x; e < nr; e += MV_NT) W[e] = d.A[e];
     __syncthreads();
 
-    // 1. partial pivoting (rows already chosen are looked up in I)
+    // 1. partial pivoting; only the columns after j are updated (earlier ones are
+    // never read again)
     for (int j = 0; j < r; ++j) {
-        double v = -1.0;
+        unsigned long long kmax = 0ull;
         long long bi = LLONG_MAX;
         for (int i = threadIdx.x; i < n; i += MV_NT) {
-            bool chosen = false;
-            for (int t = 0; t < j; ++t) chosen |= (I[t] == i);
-            const double a = chosen ? -1.0 : fabs(W[(long long)i * r + j]);
-            if (a > v || (a == v && i < bi)) {
-                v = a;
+            if ((chosen[i >> 5] >> (i & 31)) & 1u) continue;
+            const unsigned long long k = absbits(W[(long long)i * r + j]) + 1ull;  // 0 marks "no row"
+            if (k > kmax) {  // i grows per thread, so equal keys keep the first
+                kmax = k;
                 bi = i;
             }
         }
-        block_argmax(v, bi, sv, si);
+        block_argmax_u(kmax, bi, sk, si);
         const int p = (int)bi;
-        if (threadIdx.x == 0) I[j] = p;
+        if (threadIdx.x == 0) {
+            I[j] = p;
+            chosen[p >> 5] |= 1u << (p & 31);
+        }
         __syncthreads();
         const double wp = W[(long long)p * r + j];
         if (wp != 0.0) {
             for (int i = threadIdx.x; i < n; i += MV_NT) {
-                bool chosen = false;
-                for (int t = 0; t <= j; ++t) chosen |= (I[t] == i);
-                if (chosen) continue;
+                if ((chosen[i >> 5] >> (i & 31)) & 1u) continue;
                 double *wi = W + (long long)i * r;
                 const double f = wi[j] / wp;
-                for (int c = 0; c < r; ++c) wi[c] = fma(-f, W[(long long)p * r + c], wi[c]);
+                for (int c = j + 1; c < r; ++c) wi[c] = fma(-f, W[(long long)p * r + c], wi[c]);
             }
         }
         __syncthreads();
@@ -151,17 +160,17 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, doubl
     // 3. swaps
     int it = 0;
     for (; it < max_iters; ++it) {
-        double v = -1.0;
+        unsigned long long kmax = 0ull;
         long long bi = LLONG_MAX;
         for (long long e = threadIdx.x; e < nr; e += MV_NT) {
-            const double a = fabs(B[e]);
-            if (a > v) {  // e grows per thread, so equal values keep the first
-                v = a;
+            const unsigned long long k = absbits(B[e]);
+            if (k > kmax || bi == LLONG_MAX) {  // e grows per thread, so equal keys keep the first
+                kmax = k;
                 bi = e;
             }
         }
-        block_argmax(v, bi, sv, si);
-        if (!(v > 1.0 + delta)) break;
+        block_argmax_u(kmax, bi, sk, si);
+        if (!(__longlong_as_double((long long)kmax) > 1.0 + delta)) break;
         const int i0 = (int)(bi / r), j0 = (int)(bi - (long long)i0 * r);
         for (int c = threadIdx.x; c < r; c += MV_NT) row[c] = B[(long long)i0 * r + c] - (c == j0 ? 1.0 : 0.0);
         __syncthreads();

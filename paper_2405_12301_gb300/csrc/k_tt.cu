@@ -284,29 +284,61 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
     }
     __syncthreads();
     const int n = pk + (pk & 1);  // round-robin over an even count; index pk (odd case) is a bye
+    const int npairs = n / 2;
     const double tol = 8.0 * (double)max(pk, q) * DBL_EPSILON;  // cosine below which a pair counts as orthogonal
+    // per round: the pairs' dot products (a warp per pair), their rotations (a
+    // lane per pair: the square roots and divisions run once per pair, not on
+    // every lane of a warp), then the rotations themselves (a warp per pair)
+    __shared__ double s_a[TT_KMAX / 2], s_b[TT_KMAX / 2], s_c[TT_KMAX / 2], s_cs[TT_KMAX / 2], s_sn[TT_KMAX / 2];
+    __shared__ int s_uv[TT_KMAX / 2][2];
     for (int sweep = 0; sweep < 60 && n > 1; ++sweep) {
         if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
         for (int round = 0; round < n - 1; ++round) {
-            for (int slot = warp; slot < n / 2; slot += TT_NW) {
-                auto idx = [&](int t) { return t == 0 ? 0 : 1 + (t - 1 + round) % (n - 1); };
-                int u = idx(slot), v = idx(n - 1 - slot);
-                if (u >= pk || v >= pk) continue;
-                double *mu = M + u * ldm, *mv = M + v * ldm;
+            auto idx = [&](int t) { return t == 0 ? 0 : 1 + (t - 1 + round) % (n - 1); };
+            for (int slot = warp; slot < npairs; slot += TT_NW) {
+                const int u = idx(slot), v = idx(n - 1 - slot);
                 double a = 0.0, bb = 0.0, c = 0.0;
-                for (int i = lane; i < q; i += 32) {
-                    a = fma(mu[i], mu[i], a);
-                    bb = fma(mv[i], mv[i], bb);
-                    c = fma(mu[i], mv[i], c);
+                if (u < pk && v < pk) {
+                    const double *mu = M + u * ldm, *mv = M + v * ldm;
+                    for (int i = lane; i < q; i += 32) {
+                        a = fma(mu[i], mu[i], a);
+                        bb = fma(mv[i], mv[i], bb);
+                        c = fma(mu[i], mv[i], c);
+                    }
+                    a = warp_sum_d(a);
+                    bb = warp_sum_d(bb);
+                    c = warp_sum_d(c);
                 }
-                a = warp_sum_d(a);
-                bb = warp_sum_d(bb);
-                c = warp_sum_d(c);
-                if (c == 0.0 || !(fabs(c) > tol * sqrt(a * bb))) continue;
-                const double zeta = (bb - a) / (2.0 * c);
-                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = cs * t;
+                if (lane == 0) {
+                    s_a[slot] = a;
+                    s_b[slot] = bb;
+                    s_c[slot] = c;
+                    s_uv[slot][0] = u;
+                    s_uv[slot][1] = v;
+                }
+            }
+            __syncthreads();
+            for (int slot = threadIdx.x; slot < npairs; slot += TT_NT) {
+                const double a = s_a[slot], bb = s_b[slot], c = s_c[slot];
+                double cs = 1.0, sn = 0.0;
+                if (c != 0.0 && fabs(c) > tol * sqrt(a * bb)) {
+                    const double zeta = (bb - a) / (2.0 * c);
+                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                    cs = 1.0 / sqrt(fma(t, t, 1.0));
+                    sn = cs * t;
+                    rotated = 1;
+                }
+                s_cs[slot] = cs;
+                s_sn[slot] = sn;
+            }
+            __syncthreads();
+            for (int slot = warp; slot < npairs; slot += TT_NW) {
+                const double sn = s_sn[slot];
+                if (sn == 0.0) continue;
+                const double cs = s_cs[slot];
+                const int u = s_uv[slot][0], v = s_uv[slot][1];
+                double *mu = M + u * ldm, *mv = M + v * ldm;
                 for (int i = lane; i < q; i += 32) {
                     const double x = mu[i], y = mv[i];
                     mu[i] = cs * x - sn * y;
@@ -318,7 +350,6 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
                     vu[i] = cs * x - sn * y;
                     vv[i] = sn * x + cs * y;
                 }
-                if (lane == 0) rotated = 1;
             }
             __syncthreads();
         }

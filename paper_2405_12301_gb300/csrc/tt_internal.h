@@ -89,6 +89,7 @@ cudaError_t launch_tt_gemm_tr(const GemmDesc *d, int n, cudaStream_t s);
 
 // ---- batched maxvol (k_maxvol.cu)
 constexpr int MV_RMAX = 64;
+constexpr int MV_NMAX = 1 << 16;  // rows of a maxvol matrix
 struct MaxvolDesc {
     const double *A;   // n x r row-major
     double *B;         // n x r: A A[I]^{-1} on exit

@@ -160,24 +160,31 @@ def test_3d_384_cube_run_to_half_time(W):
 
 def test_2d_quadrant_1024_and_2048_runs(W):
     """Config 3 at its own sizes: 1024^2 in FP64 and FP32-bulk and 2048^2 in
-    FP32-bulk, transmissive, to t = 0.3.  FP32-bulk stays within a bounded
-    distance of FP64 (the 256^2 bound), the states stay physical, and the
-    mass sums change only by the boundary fluxes (bounded by the run length)."""
+    FP32-bulk, transmissive, to t = 0.3.  Transmissive sides let mass in where the
+    corner states move inwards (SW, NW, SE), so the physical mass M = sum(rho) h^2
+    grows; checked: FP32-bulk and FP64 give the same M and a close state, M at
+    2048^2 agrees with 1024^2, and |M - M0| stays under t x perimeter x max |rho u|."""
     T = O.TRANSMISSIVE
+    masses = {}
     for N in (1024, 2048):
         n = (N, N)
+        h2 = (1.0 / N) ** 2
         cfg = O.Cfg(dim=2, n=n, bc=((T, T), (T, T)))
         U0 = I.quadrant_riemann(n)
-        m0 = O.sums(cfg, U0)
+        M0 = O.sums(cfg, U0)[0] * h2
         u32, st32 = gpu_run(W, cfg, U0, 0.3, W.FP32_BULK)
         assert np.isfinite(u32).all() and u32[0].min() > 0
-        m32 = O.sums(cfg, u32)
-        line = "quadrant %d^2: %d steps FP32-bulk; mass %.6f -> %.6f" % (N, st32, m0[0], m32[0])
+        M32 = O.sums(cfg, u32)[0] * h2
+        masses[N] = M32
+        line = "quadrant %d^2: %d steps FP32-bulk; M %.6f -> %.6f" % (N, st32, M0, M32)
         if N == 1024:
             u64, st64 = gpu_run(W, cfg, U0, 0.3, W.FP64)
+            M64 = O.sums(cfg, u64)[0] * h2
             d = np.abs(u32[0] - u64[0]).mean() / np.abs(u64[0]).mean()
-            line += "; FP64 %d steps, FP32-bulk vs FP64 L1(rho)/mean = %.2e" % (st64, d)
+            line += "; FP64 %d steps, M %.9f; FP32-bulk vs FP64 L1(rho)/mean = %.2e" % (st64, M64, d)
             assert d < 1e-4
+            assert abs(M32 - M64) <= 1e-6 * M64
         print(line)
-        # the corner states move outwards at most ~1.5 (speeds < |u| + a): mass leaves only near the edges
-        assert abs(m32[0] - m0[0]) < 0.1 * m0[0]
+        rho_u_max = max(0.5323 * 1.206, 0.138 * 1.206 * 2 ** 0.5)
+        assert abs(M32 - M0) <= 0.3 * 4.0 * rho_u_max
+    assert abs(masses[2048] - masses[1024]) <= 1e-2 * masses[1024]
