@@ -38,6 +38,18 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Sum over the 8-lane group of a lane (lanes 8g .. 8g+7).  The update loops
+// below give each column of a reflector update to one 8-lane group (4 columns
+// per warp, a lane every 8th row), so a column's dot product costs 3 shuffle
+// adds instead of 5 and every FP64 instruction serves 4 columns.
+__device__ __forceinline__ double group8_sum(double v)
+{
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+    return v;
+}
+
 // Householder vector of x = (x0, y) with ||y||^2 = sig: H = I - tau v v^T,
 // v = (1, y / (x0 - beta)), H x = (beta, 0).  sig == 0 gives tau = 0.
 __device__ __forceinline__ void householder(double x0, double sig, double &beta, double &tau, double &scale)
@@ -69,7 +81,7 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
     double *B = sm;                       // sub-block, column-major [k][ldb]
     double *R = B + (size_t)k * ldb;      // running R, column-major [k][ldr]
     double *ts = R + (size_t)k * ldr;     // taus of the current sub-block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sub = lane & 7;
     const long long r0 = (long long)chunk * d.chunk_rows;
     const long long r1 = min(d.m, r0 + d.chunk_rows);
 
@@ -105,14 +117,18 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
                 const double tau = ts[j];
                 if (tau != 0.0) {
                     const double *v = B + j * ldb;
-                    for (int c = j + 1 + warp; c < k; c += TT_NW) {
-                        double *col = B + c * ldb;
+                    for (int c0 = j + 1 + warp * 4; c0 < k; c0 += TT_NW * 4) {
+                        const int c = c0 + grp;
+                        const bool ok = c < k;
+                        double *col = B + (ok ? c : 0) * ldb;
                         double w = 0.0;
-                        for (int i = j + 1 + lane; i < bs; i += 32) w = fma(v[i], col[i], w);
-                        w = (warp_sum_d(w) + col[j]) * tau;
-                        for (int i = j + 1 + lane; i < bs; i += 32) col[i] = fma(-v[i], w, col[i]);
+                        if (ok)
+                            for (int i = j + 1 + sub; i < bs; i += 8) w = fma(v[i], col[i], w);
+                        w = (group8_sum(w) + (ok ? col[j] : 0.0)) * tau;
+                        if (ok)
+                            for (int i = j + 1 + sub; i < bs; i += 8) col[i] = fma(-v[i], w, col[i]);
                         __syncwarp();
-                        if (lane == 0) col[j] -= w;
+                        if (ok && sub == 0) col[j] -= w;
                     }
                 }
                 __syncthreads();
@@ -142,14 +158,18 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
                 const double tau = ts[j];
                 if (tau != 0.0) {
                     const double *y = B + j * ldb;
-                    for (int c = j + 1 + warp; c < k; c += TT_NW) {
-                        double *col = B + c * ldb;
+                    for (int c0 = j + 1 + warp * 4; c0 < k; c0 += TT_NW * 4) {
+                        const int c = c0 + grp;
+                        const bool ok = c < k;
+                        double *col = B + (ok ? c : 0) * ldb;
                         double w = 0.0;
-                        for (int i = lane; i < bs; i += 32) w = fma(y[i], col[i], w);
-                        w = (warp_sum_d(w) + R[c * ldr + j]) * tau;
-                        for (int i = lane; i < bs; i += 32) col[i] = fma(-y[i], w, col[i]);
+                        if (ok)
+                            for (int i = sub; i < bs; i += 8) w = fma(y[i], col[i], w);
+                        w = (group8_sum(w) + (ok ? R[c * ldr + j] : 0.0)) * tau;
+                        if (ok)
+                            for (int i = sub; i < bs; i += 8) col[i] = fma(-y[i], w, col[i]);
                         __syncwarp();
-                        if (lane == 0) R[c * ldr + j] -= w;
+                        if (ok && sub == 0) R[c * ldr + j] -= w;
                     }
                 }
                 __syncthreads();
@@ -179,7 +199,7 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
     double *Z = Y + (size_t)k * ldb;       // output block, column-major [p][ldb]
     double *X = Z + (size_t)p * ldb;       // running top rows, column-major [p][ldx]
     double *ts = X + (size_t)p * ldx;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sub = lane & 7;
     const long long r0 = (long long)chunk * d.chunk_rows;
     const long long r1 = min(d.m, r0 + d.chunk_rows);
     const int nsub = (int)((r1 - r0 + b - 1) / b);
@@ -208,19 +228,23 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
         for (int e = threadIdx.x; e < bs * p; e += TT_NT) Z[(e / bs) * ldb + e % bs] = 0.0;
         for (int j = threadIdx.x; j < k; j += TT_NT) ts[j] = d.tau[((long long)chunk * d.sub_per_chunk + s) * k + j];
         __syncthreads();
-        for (int q = warp; q < p; q += TT_NW) {
-            double *zq = Z + q * ldb;
-            double *xq = X + q * ldx;
+        for (int q0 = warp * 4; q0 < p; q0 += TT_NW * 4) {
+            const int q = q0 + grp;
+            const bool ok = q < p;
+            double *zq = Z + (ok ? q : 0) * ldb;
+            double *xq = X + (ok ? q : 0) * ldx;
             for (int j = k - 1; j >= 0; --j) {
                 const double tau = ts[j];
                 if (tau == 0.0) continue;
                 const double *y = Y + j * ldb;
                 double w = 0.0;
-                for (int i = lane; i < bs; i += 32) w = fma(y[i], zq[i], w);
-                w = (warp_sum_d(w) + xq[j]) * tau;
-                for (int i = lane; i < bs; i += 32) zq[i] = fma(-y[i], w, zq[i]);
+                if (ok)
+                    for (int i = sub; i < bs; i += 8) w = fma(y[i], zq[i], w);
+                w = (group8_sum(w) + (ok ? xq[j] : 0.0)) * tau;
+                if (ok)
+                    for (int i = sub; i < bs; i += 8) zq[i] = fma(-y[i], w, zq[i]);
                 __syncwarp();
-                if (lane == 0) xq[j] -= w;
+                if (ok && sub == 0) xq[j] -= w;
                 __syncwarp();
             }
         }
@@ -239,18 +263,22 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
     }
     for (int j = threadIdx.x; j < k; j += TT_NT) ts[j] = d.tau[(long long)chunk * d.sub_per_chunk * k + j];
     __syncthreads();
-    for (int q = warp; q < p; q += TT_NW) {
-        double *zq = Z + q * ldb;
+    for (int q0 = warp * 4; q0 < p; q0 += TT_NW * 4) {
+        const int q = q0 + grp;
+        const bool ok = q < p;
+        double *zq = Z + (ok ? q : 0) * ldb;
         for (int j = kk - 1; j >= 0; --j) {
             const double tau = ts[j];
             if (tau == 0.0) continue;
             const double *v = Y + j * ldb;
             double w = 0.0;
-            for (int i = j + 1 + lane; i < b1; i += 32) w = fma(v[i], zq[i], w);
-            w = (warp_sum_d(w) + zq[j]) * tau;
-            for (int i = j + 1 + lane; i < b1; i += 32) zq[i] = fma(-v[i], w, zq[i]);
+            if (ok)
+                for (int i = j + 1 + sub; i < b1; i += 8) w = fma(v[i], zq[i], w);
+            w = (group8_sum(w) + (ok ? zq[j] : 0.0)) * tau;
+            if (ok)
+                for (int i = j + 1 + sub; i < b1; i += 8) zq[i] = fma(-v[i], w, zq[i]);
             __syncwarp();
-            if (lane == 0) zq[j] -= w;
+            if (ok && sub == 0) zq[j] -= w;
             __syncwarp();
         }
     }
