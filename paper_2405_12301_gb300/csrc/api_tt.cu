@@ -400,7 +400,7 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
         const weno_maxvol_problem &P = probs[i];
         if (P.r < 1 || P.r > MV_RMAX || P.n < P.r || P.n > MV_NMAX || !P.A || !P.B || !P.idx)
             return fail(h, WENO_ERR_ARG, "weno_maxvol: need 1 <= r <= 64, r <= n <= 65536 and non-null A, B, idx");
-        w_total += (((size_t)P.n * P.r + 31) & ~size_t(31));
+        w_total += (((size_t)P.n * P.r + 31) & ~size_t(31)) + (((size_t)P.r * P.r + 31) & ~size_t(31));
         max_r = std::max(max_r, (int)P.r);
     }
     const size_t off_desc = 0;
@@ -413,8 +413,9 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
     double *w = (double *)(base + off_w);
     for (int i = 0; i < n_probs; ++i) {
         const weno_maxvol_problem &P = probs[i];
-        ds[i] = MaxvolDesc{P.A, P.B, w, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
-        w += (((size_t)P.n * P.r + 31) & ~size_t(31));
+        double *minv = w + (((size_t)P.n * P.r + 31) & ~size_t(31));
+        ds[i] = MaxvolDesc{P.A, P.B, w, minv, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
+        w = minv + (((size_t)P.r * P.r + 31) & ~size_t(31));
     }
     MaxvolDesc *dd = (MaxvolDesc *)(base + off_desc);
     CK(h, cudaMemcpyAsync(dd, ds.data(), sizeof(MaxvolDesc) * n_probs, cudaMemcpyHostToDevice, h->stream));
@@ -445,7 +446,7 @@ struct XProb {
     int *right0 = nullptr, *left1 = nullptr, *right1 = nullptr, *left2 = nullptr;
     double *M0 = nullptr, *M1 = nullptr, *MR2 = nullptr, *MR1 = nullptr;
     double *Q0 = nullptr, *Q1 = nullptr, *QR2 = nullptr, *QR1 = nullptr;
-    double *B1 = nullptr, *BR = nullptr, *Wmv = nullptr;
+    double *B1 = nullptr, *BR = nullptr, *Wmv = nullptr, *Minv = nullptr;
     int *idx = nullptr;
     QRPlan q0, q1, qr2, qr1;
 };
@@ -507,6 +508,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
             const size_t mk = std::max({n1 * r1, r1 * n2 * r2, 5 * n3 * r2, n2 * r2 * r1});
             x.BR = bp.take<double>(mk);
             x.Wmv = bp.take<double>(mk);
+            x.Minv = bp.take<double>(std::max(r1, r2) * std::max(r1, r2));
             x.idx = bp.take<int>(std::max(r1, r2));
             qr_take(bp, x.q0);
             qr_take(bp, x.q1);
@@ -593,7 +595,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
             QRPlan &q = x.*qp;
             double *Bout = b_is_core0 ? probs[i].core[0] : x.*Bp;
             int *st = status + 2 * ((size_t)mv_call * np + i);
-            md[i] = MaxvolDesc{x.*Qp, Bout, x.Wmv, x.idx, st, st + 1, (int)q.m, q.k};
+            md[i] = MaxvolDesc{x.*Qp, Bout, x.Wmv, x.Minv, x.idx, st, st + 1, (int)q.m, q.k};
             mr = std::max(mr, q.k);
         }
         MaxvolDesc *dd = (MaxvolDesc *)slot(3);

@@ -1,6 +1,7 @@
 // k_maxvol.cu -- batched maxvol (the maximum-volume row selection that picks
-// the cross indices of TT-cross, Sec. 3 "TT-cross Interpolation"), FP64, one
-// CTA per n x r matrix (r <= 64):
+// the cross indices of TT-cross, Sec. 3 "TT-cross Interpolation"), FP64, three
+// launches per batch (phases 1 and 3 one CTA per n x r matrix, r <= 64; the
+// product of phase 2 spread over many CTAs):
 //   1. the r pivot rows of Gaussian elimination with partial pivoting on a
 //      working copy W (largest remaining |W[i][j]| of column j, ties to the
 //      smaller row);
@@ -8,8 +9,8 @@
 //      pivoting in shared memory;
 //   3. while max |B[i][j]| > 1 + delta (ties to the first entry in row-major
 //      order): row i replaces I[j] and B -= B[:, j] (B[i, :] - e_j) / B[i][j].
-// W and B live in global memory (L2-resident); every pass is one block-wide
-// argmax and one row-parallel update.
+// W and B live in global memory (L2-resident); every pass of phases 1 and 3 is
+// one block-wide argmax and one row-parallel update.
 #include <climits>
 
 #include "weno_dev.cuh"
@@ -57,7 +58,8 @@ __device__ __forceinline__ void block_argmax_u(unsigned long long &k, long long 
 
 size_t maxvol_smem(int r) { return sizeof(double) * (size_t)r * (2 * r + 1) + sizeof(int) * (size_t)(r + 1); }
 
-__global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, double delta, int max_iters)
+// Phase 1 and the inverse: one CTA per matrix.
+__global__ void __launch_bounds__(MV_NT) k_maxvol_pivot(const MaxvolDesc *descs)
 {
     const MaxvolDesc d = descs[blockIdx.x];
     const int n = d.n, r = d.r;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, doubl
     __shared__ long long si[MV_NW];
     __shared__ int s_fail;
     __shared__ unsigned chosen[MV_NMAX / 32];  // rows already picked by the pivoting
-    double *W = d.W, *B = d.B;
+    double *W = d.W;
     const long long nr = (long long)n * r;
     if (threadIdx.x == 0) s_fail = 0;
     for (int e = threadIdx.x; e < (n + 31) / 32; e += MV_NT) chosen[e] = 0u;
@@ -143,20 +145,47 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, doubl
         }
         __syncthreads();
     }
-    if (s_fail) {
-        if (threadIdx.x == 0) d.status[0] = 1;
-        return;
+    if (threadIdx.x == 0) d.status[0] = s_fail;
+    if (s_fail) return;
+    for (int e = threadIdx.x; e < r * r; e += MV_NT) {
+        const int k = e / r, c = e - k * r;
+        d.Minv[e] = G[k * 2 * r + r + c];
     }
-    for (long long e = threadIdx.x; e < nr; e += MV_NT) {
+    for (int j = threadIdx.x; j < r; j += MV_NT) d.idx[j] = I[j];
+}
+
+// B = A A[I]^{-1}: the n x r by r x r product, spread over many CTAs per matrix.
+__global__ void k_maxvol_b(const MaxvolDesc *descs)
+{
+    const MaxvolDesc &d = descs[blockIdx.y];
+    if (d.status[0]) return;
+    const int r = d.r;
+    const long long nr = (long long)d.n * r;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long long)gridDim.x * blockDim.x) {
         const long long i = e / r;
         const int c = (int)(e - i * r);
         const double *ai = d.A + i * r;
-        double s = 0.0;
-        for (int k = 0; k < r; ++k) s = fma(ai[k], G[k * 2 * r + r + c], s);
-        B[e] = s;
+        double acc = 0.0;
+        for (int k = 0; k < r; ++k) acc = fma(ai[k], d.Minv[k * r + c], acc);
+        d.B[e] = acc;
     }
-    __syncthreads();
+}
 
+// Phase 3, the swaps: one CTA per matrix.
+__global__ void __launch_bounds__(MV_NT) k_maxvol_swap(const MaxvolDesc *descs, double delta, int max_iters)
+{
+    const MaxvolDesc d = descs[blockIdx.x];
+    if (d.status[0]) return;
+    const int n = d.n, r = d.r;
+    extern __shared__ double sm[];
+    double *row = sm;                                // [r]
+    int *I = reinterpret_cast<int *>(row + r);       // [r]
+    __shared__ unsigned long long sk[MV_NW];
+    __shared__ long long si[MV_NW];
+    double *B = d.B;
+    const long long nr = (long long)n * r;
+    for (int j = threadIdx.x; j < r; j += MV_NT) I[j] = d.idx[j];
+    __syncthreads();
     // 3. swaps
     int it = 0;
     for (; it < max_iters; ++it) {
@@ -192,15 +221,16 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol(const MaxvolDesc *descs, doubl
 
 cudaError_t launch_maxvol(const MaxvolDesc *d, int n, int max_r, double delta, int max_iters, cudaStream_t s)
 {
-    const size_t smem = maxvol_smem(max_r);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_maxvol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_maxvol_pivot, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)maxvol_smem(MV_RMAX));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_maxvol<<<n, MV_NT, smem, s>>>(d, delta, max_iters);
+    k_maxvol_pivot<<<n, MV_NT, maxvol_smem(max_r), s>>>(d);
+    k_maxvol_b<<<dim3(64, n), 256, 0, s>>>(d);
+    k_maxvol_swap<<<n, MV_NT, sizeof(double) * max_r + sizeof(int) * (max_r + 1), s>>>(d, delta, max_iters);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,7 @@ struct MaxvolDesc {
     const double *A;   // n x r row-major
     double *B;         // n x r: A A[I]^{-1} on exit
     double *W;         // n x r scratch
+    double *Minv;      // r x r scratch: A[I]^{-1} of the pivot rows
     int *idx;          // r selected rows
     int *status;       // 0 ok, 1 A[I] singular after pivoting
     int *swaps;
