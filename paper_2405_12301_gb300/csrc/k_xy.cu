@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
         T fp[NF], fm[NF];
         if constexpr (BULK) {
-            if (dirx) split_flux_diff<D, 0>(q, ref, alX, a.gm1_f, fp, fm);
-            else split_flux_diff<D, 1>(q, ref, alY, a.gm1_f, fp, fm);
+            if (dirx) split_flux_diff<D, 0, true>(q, ref, alX, a.gm1_f, fp, fm);
+            else split_flux_diff<D, 1, true>(q, ref, alY, a.gm1_f, fp, fm);
         } else {
-            if (dirx) split_flux_f64<D, 0>(q, alX, gm1, fp, fm);
-            else split_flux_f64<D, 1>(q, alY, gm1, fp, fm);
+            if (dirx) split_flux_f64<D, 0, true>(q, alX, gm1, fp, fm);
+            else split_flux_f64<D, 1, true>(q, alY, gm1, fp, fm);
         }
         if (dirx) {
             const int o = ly * BXP + (lx + 3);
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
 
     // ---- phase W: own left x face and bottom y face for every component, plus
     // one of the remaining faces (top of the tile's top row, right of its last column)
-    const T eps = BULK ? (T)a.eps_f : (T)a.eps;
+    // the shared arrays hold 2 f(+/-): reconstruct with 4 eps (twice the WENO5 value)
+    const T eps = T(4) * (BULK ? (T)a.eps_f : (T)a.eps);
     auto face_x = [&](int f, int ly, int j) -> T {  // between local columns j-1 and j of row ly
         const T *P = fx + f * NXP + ly * BXP;
         const T *M = fx + (NF + f) * NXP + ly * BXP;
@@ -284,8 +285,9 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
     __syncthreads();
 
     // ---- phase C: the cell's residual -(dF/dx) - (dG/dy) and the epilogue
-    const T ihx = BULK ? (T)a.inv_h_f[0] : (T)a.inv_h[0];
-    const T ihy = BULK ? (T)a.inv_h_f[1] : (T)a.inv_h[1];
+    // face fluxes are twice F^: the halving rides on 1/h
+    const T ihx = T(0.5) * (BULK ? (T)a.inv_h_f[0] : (T)a.inv_h[0]);
+    const T ihy = T(0.5) * (BULK ? (T)a.inv_h_f[1] : (T)a.inv_h[1]);
     T r[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
                     split_f64(un[f], hn, ln);
                     dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
                 }
-                a.Uout[f * N + cell] = uk[f] + f32_to_f64(dl);
+                a.Uout[f * N + cell] = uk[f] + (double)dl;  // F2F on the FP64 pipe (it has room here)
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<D>(qn, a.gamma_f, bad);

@@ -219,7 +219,10 @@ __device__ __forceinline__ void weno5_slide(const T *p, int s, T eps, T *out, in
 
 // Plain FP64 Euler flux in direction DIR (Sec. 2.1) and its LF split
 // f(+/-) = (F +/- alpha U) / 2 (Sec. 2.2).
-template <int D, int DIR>
+// TWICE: return 2 f(+/-) = F +/- alpha U (one FMA each, no halving); the
+// caller then reconstructs with 4 eps, which gives exactly twice the WENO5
+// value of f(+/-) (scaling by 2 commutes with every rounding), and halves once.
+template <int D, int DIR, bool TWICE = false>
 __device__ __forceinline__ void split_flux_f64(const double *q, double alpha, double gm1, double *fp, double *fm)
 {
     constexpr int NF = D + 2;
@@ -240,8 +243,13 @@ __device__ __forceinline__ void split_flux_f64(const double *q, double alpha, do
     F[D + 1] = u[DIR] * (q[D + 1] + p);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        fp[f] = 0.5 * (F[f] + alpha * q[f]);
-        fm[f] = 0.5 * (F[f] - alpha * q[f]);
+        if (TWICE) {
+            fp[f] = fma(alpha, q[f], F[f]);
+            fm[f] = fma(-alpha, q[f], F[f]);
+        } else {
+            fp[f] = 0.5 * (F[f] + alpha * q[f]);
+            fm[f] = 0.5 * (F[f] - alpha * q[f]);
+        }
     }
 }
 
@@ -287,7 +295,7 @@ __device__ __forceinline__ void diff_from_ref(const double *q, const RefState<D>
 // using only exact product-difference identities
 //   d(ab) = da * b + a_ref * db,  du = (dm - u_ref drho) / rho,
 // so every rounding error is relative to the differences, not to the state.
-template <int D, int DIR>
+template <int D, int DIR, bool TWICE = false>
 __device__ __forceinline__ void split_flux_diff(const float *dq, const RefState<D> &r, float alpha, float gm1,
                                                 float *fp, float *fm)
 {
@@ -311,8 +319,13 @@ __device__ __forceinline__ void split_flux_diff(const float *dq, const RefState<
     dF[D + 1] = du[DIR] * (r.H + dH) + r.u[DIR] * dH;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        fp[f] = 0.5f * (dF[f] + alpha * dq[f]);
-        fm[f] = 0.5f * (dF[f] - alpha * dq[f]);
+        if (TWICE) {  // 2 f(+/-), see split_flux_f64
+            fp[f] = fmaf(alpha, dq[f], dF[f]);
+            fm[f] = fmaf(-alpha, dq[f], dF[f]);
+        } else {
+            fp[f] = 0.5f * (dF[f] + alpha * dq[f]);
+            fm[f] = 0.5f * (dF[f] - alpha * dq[f]);
+        }
     }
 }
 
