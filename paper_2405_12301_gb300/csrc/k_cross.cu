@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
     T *Cref = C + 5 * CP * CS;                // [5][CS]     chunk reference row (FP32, fd == mode)
     T *fixv = Cref + 5 * CS;                  // [5][CS]     the work item's fixed vector
     __shared__ long long s_item;
-    const T eps = (T)A.eps;
+    const T eps = T(4) * (T)A.eps;  // split fluxes are formed doubled: 4 eps gives twice the WENO5 value
     const double gm1 = A.gamma - 1.0;
     const T *vecs = reinterpret_cast<const T *>(A.vecs);
 
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
         const T *var = vecs + (role == 2 ? S.rvec_off : S.lvec_off);  // the varying side's vectors
         const int nsv = role == 2 ? S.nsr : S.nsl;
         const T alpha = (T)in.alpha;
-        const T ih = (T)(1.0 / in.h[fd]);
+        const T ih = (T)(0.5 / in.h[fd]);  // halves the doubled face fluxes
         {   // fixed vector (centre) of this work item
             const T *src = vecs + (role == 2 ? S.lvec_off + (j * S.nsl + (S.nsl == 7 ? 3 : 0)) * 5 * VP
                                              : S.rvec_off + (j * S.nsr + (S.nsr == 7 ? 3 : 0)) * 5 * VP);
@@ -314,9 +314,9 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
                         double qd[5], a5[5], b5[5];
 #pragma unroll
                         for (int f = 0; f < 5; ++f) qd[f] = q7[f][k];
-                        if (fd == 0) split_flux_f64<3, 0>(qd, (double)alpha, gm1, a5, b5);
-                        else if (fd == 1) split_flux_f64<3, 1>(qd, (double)alpha, gm1, a5, b5);
-                        else split_flux_f64<3, 2>(qd, (double)alpha, gm1, a5, b5);
+                        if (fd == 0) split_flux_f64<3, 0, true>(qd, (double)alpha, gm1, a5, b5);
+                        else if (fd == 1) split_flux_f64<3, 1, true>(qd, (double)alpha, gm1, a5, b5);
+                        else split_flux_f64<3, 2, true>(qd, (double)alpha, gm1, a5, b5);
 #pragma unroll
                         for (int f = 0; f < 5; ++f) { fp7[f][k] = a5[f]; fm7[f][k] = b5[f]; }
                     }
@@ -341,9 +341,9 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
                         float dq[5], a5[5], b5[5];
 #pragma unroll
                         for (int f = 0; f < 5; ++f) dq[f] = q7[f][k];
-                        if (fd == 0) split_flux_diff<3, 0>(dq, rs, alpha, (float)gm1, a5, b5);
-                        else if (fd == 1) split_flux_diff<3, 1>(dq, rs, alpha, (float)gm1, a5, b5);
-                        else split_flux_diff<3, 2>(dq, rs, alpha, (float)gm1, a5, b5);
+                        if (fd == 0) split_flux_diff<3, 0, true>(dq, rs, alpha, (float)gm1, a5, b5);
+                        else if (fd == 1) split_flux_diff<3, 1, true>(dq, rs, alpha, (float)gm1, a5, b5);
+                        else split_flux_diff<3, 2, true>(dq, rs, alpha, (float)gm1, a5, b5);
 #pragma unroll
                         for (int f = 0; f < 5; ++f) { fp7[f][k] = a5[f]; fm7[f][k] = b5[f]; }
                     }

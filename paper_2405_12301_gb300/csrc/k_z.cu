@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     };
     auto flux_store = [&](const T *q, int lx, int lz) {
         T fp[NF], fm[NF];
-        if constexpr (BULK) split_flux_diff<3, 2>(q, ref, al, a.gm1_f, fp, fm);
-        else split_flux_f64<3, 2>(q, al, gm1, fp, fm);
+        if constexpr (BULK) split_flux_diff<3, 2, true>(q, ref, al, a.gm1_f, fp, fm);
+        else split_flux_f64<3, 2, true>(q, al, gm1, fp, fm);
         const int o = (lz + 3) * TX + lx;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     }
     __syncthreads();
 
-    const T eps = BULK ? (T)a.eps_f : (T)a.eps;
+    // the shared arrays hold 2 f(+/-): reconstruct with 4 eps (twice the WENO5 value)
+    const T eps = T(4) * (BULK ? (T)a.eps_f : (T)a.eps);
     auto face_z = [&](int f, int lx, int j) -> T {  // between local planes j-1 and j of column lx
         const T *P = fz + f * NZP + lx;
         const T *M = fz + (NF + f) * NZP + lx;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     }
     __syncthreads();
 
-    const T ihz = BULK ? (T)a.inv_h_f[2] : (T)a.inv_h[2];
+    const T ihz = T(0.5) * (BULK ? (T)a.inv_h_f[2] : (T)a.inv_h[2]);  // face fluxes are twice F^
     const T *acc = reinterpret_cast<const T *>(a.acc);
     T r[NF];
 #pragma unroll
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
                     split_f64(un[f], hn, ln);
                     dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
                 }
-                a.Uout[f * N + cell] = uk[f] + f32_to_f64(dl);
+                a.Uout[f * N + cell] = uk[f] + (double)dl;
                 qn[f] = hk[f] + (lk[f] + dl);
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
