@@ -151,7 +151,30 @@ def cpu_baseline(seconds=12.0):
             break
     value = n[0] * n[1] * 3 * steps / el / 1e6
     return {"value": value, "unit": "Mcell-stage/s", "cores": 1, "kind": "oracle",
-            "sample": "%d SSP-RK3 steps of the 2D density wave on 256^2 (%.1f s, 1 thread)" % (steps, el)}
+            "sample": "%d SSP-RK3 steps of the 2D density wave on 256^2 (%.1f s, 1 thread)" % (steps, el),
+            "host": host_info()}
+
+
+def host_info():
+    """CPU model and the cores this process may run on (the oracle uses one)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.machine()
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except AttributeError:
+        avail = os.cpu_count()
+    return {"cpu": model, "cores_available": avail}
 
 
 def reference_arm(args, rank):
@@ -182,7 +205,8 @@ def reference_arm(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["name"], "sample_grid": list(n)},
-        "cpu_baseline": {"value": v, "unit": "Mcell-stage/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "Mcell-stage/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_info()},
         "e2e": {"value": v, "unit": "Mcell-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
