@@ -16,11 +16,12 @@
 //                 scales with the variation along the stencil);
 //   k_cross       persistent; a work item fixes one index of the side the
 //                 stencil does not move (r for fd <= m, l for fd > m).  For each
-//                 chunk of 64 samples it contracts the core rows G_m(i) with that
-//                 fixed vector once into shared memory; every sample (v, i) of
-//                 the other side's index v then needs only 7 dot products per
-//                 field, followed by the LF split fluxes at the 7 points and
-//                 WENO5(+/-) at the two interfaces of the sample.
+//                 chunk of samples (32 to 128, per variant) it contracts the
+//                 core rows G_m(i) with that fixed vector once into shared
+//                 memory; every sample (v, i) of the other side's index v
+//                 then needs only 7 dot products per field, followed by the
+//                 LF split fluxes at the 7 points and WENO5(+/-) at the two
+//                 interfaces of the sample.
 // Ghost rows (Sec. 4.5) are mapped by the boundary rule of fd.
 #include "weno_dev.cuh"
 #include "weno_internal.h"

@@ -10,8 +10,8 @@
 //     [e_j; y_j].  The chunk R factors are stacked and factored the same way
 //     by a second launch.  Reflectors overwrite the matrix; taus are kept.
 //   * k_qr_apply: Q [X; 0] for a k x p block X, replaying the reflectors of a
-//     chunk in reverse (one warp per column of X, no block barrier inside a
-//     sub-block); writes the rows through a general row map so that results
+//     chunk in reverse (eight lanes per column of X, four columns per warp,
+//     no block barrier inside a sub-block); writes the rows through a general row map so that results
 //     land directly in TT-core layout.
 //   * k_svd_jacobi: one-sided Jacobi SVD (round-robin pair ordering) of the
 //     transpose of a k x q triangular factor T: T^T V = U S gives T = V S U^T;
