@@ -176,8 +176,9 @@ int weno_sync(weno_handle h);
  *   kind 3: 1D sweep, kind 4: fused x+y kernel of a 2D grid, kind 5: z sweep
  *           of a 3D grid (3..5 end a residual: stage combination or L(U)),
  *   kind 6: wavespeed max, kind 7: step control and other small kernels,
- *   kind 0: TT-rounding QR factor/apply, kind 1: TT-rounding SVD and
- *   contractions (weno_tt_round).
+ *   kind 0: QR factor/apply (weno_tt_round, weno_tt_cross), kind 1: SVD and
+ *   contractions of weno_tt_round, maxvol, the TT-cross bookkeeping kernels;
+ *   weno_cross_eval's kernels count as kind 7.
  * ms and launches (host arrays of WENO_PROFILE_KINDS) receive the totals since
  * the last enable; *total_launches counts every kernel this handle launched
  * (graphs included) since the last enable. */
@@ -356,8 +357,9 @@ typedef struct {
     int32_t *idx;       /* device, r: receives the selected rows I */
 } weno_maxvol_problem;
 
-/* Batched maxvol, FP64, one CTA per matrix: the r pivot rows of Gaussian
- * elimination with partial pivoting, B = A A[I]^{-1}, then row swaps while
+/* Batched maxvol, FP64, one thread-block cluster per matrix: the r pivot
+ * rows of Gaussian elimination with partial pivoting, B = A A[I]^{-1}, then
+ * row swaps while
  * some |B[i][j]| > 1 + delta (each swap multiplies |det A[I]| by |B[i][j]|;
  * ties go to the first entry in row-major order) or max_iters swaps are done.
  * probs: HOST array; synchronises the stream; swaps (host, may be NULL)

@@ -417,9 +417,11 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
         ds[i] = MaxvolDesc{P.A, P.B, w, minv, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
         w = minv + (((size_t)P.r * P.r + 31) & ~size_t(31));
     }
+    maxvol_order(ds.data(), n_probs);
     MaxvolDesc *dd = (MaxvolDesc *)(base + off_desc);
     CK(h, cudaMemcpyAsync(dd, ds.data(), sizeof(MaxvolDesc) * n_probs, cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, n_probs, max_r, delta, max_iters, h->stream); }));
+    CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, n_probs, max_r, delta, max_iters, h->stream); },
+                 MV_LAUNCHES));
     std::vector<int> st(2 * n_probs);
     CK(h, cudaMemcpyAsync(st.data(), ints, sizeof(int) * 2 * n_probs, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -598,9 +600,10 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
             md[i] = MaxvolDesc{x.*Qp, Bout, x.Wmv, x.Minv, x.idx, st, st + 1, (int)q.m, q.k};
             mr = std::max(mr, q.k);
         }
+        maxvol_order(md.data(), np);
         MaxvolDesc *dd = (MaxvolDesc *)slot(3);
         CK(h, cudaMemcpyAsync(dd, md.data(), sizeof(MaxvolDesc) * np, cudaMemcpyHostToDevice, h->stream));
-        CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, np, mr, delta, 200, h->stream); }));
+        CK(h, launch(h, 1, h->stream, [&] { return launch_maxvol(dd, np, mr, delta, 200, h->stream); }, MV_LAUNCHES));
         ++mv_call;
         return WENO_OK;
     };

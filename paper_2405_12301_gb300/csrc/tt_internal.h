@@ -101,6 +101,9 @@ struct MaxvolDesc {
     int n, r;
 };
 size_t maxvol_smem(int r);
+constexpr int MV_LAUNCHES = 3;  // kernels of one launch_maxvol
+// Orders a batch largest first (n r^2), so the biggest matrices start first.
+void maxvol_order(MaxvolDesc *d, int n);
 cudaError_t launch_maxvol(const MaxvolDesc *d, int n, int max_r, double delta, int max_iters, cudaStream_t s);
 
 

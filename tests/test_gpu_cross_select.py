@@ -52,6 +52,35 @@ def test_maxvol_matches_oracle(W, H):
         assert np.abs(Bn).max() <= 1.0 + 1e-2 + 1e-10
 
 
+def test_maxvol_large_and_mixed_batch_matches_oracle(W, H):
+    """Row counts from fewer rows than a cluster has CTAs up to the 65536-row
+    limit, orthonormal inputs as the TT-cross passes them, in one batch (the
+    batch is launched largest first; results keep the caller's order)."""
+    rng = np.random.default_rng(4)
+    sizes = [(3, 3), (65536, 8), (17, 16), (15360, 32), (4097, 64), (9, 2)]
+    mats = []
+    for k, s in enumerate(sizes):
+        A = rng.standard_normal(s)
+        mats.append(np.linalg.qr(A)[0] if k % 2 else A)
+    outs = W.weno_maxvol(H, [torch.from_numpy(A).cuda() for A in mats], delta=1e-2)
+    for A, (idx, B, swaps) in zip(mats, outs):
+        Io, Bo, so = X.maxvol(A, delta=1e-2)
+        assert idx.cpu().numpy().tolist() == Io.tolist()
+        assert swaps == so
+        assert np.abs(B.cpu().numpy() - Bo).max() <= 1e-9 * max(1.0, np.abs(Bo).max())
+
+
+def test_maxvol_stops_at_max_iters(W, H):
+    rng = np.random.default_rng(5)
+    mats = [rng.standard_normal((3000, 24)) for _ in range(3)]
+    outs = W.weno_maxvol(H, [torch.from_numpy(A).cuda() for A in mats], delta=1e-2, max_iters=2)
+    for A, (idx, B, swaps) in zip(mats, outs):
+        Io, Bo, so = X.maxvol(A, delta=1e-2, max_iters=2)
+        assert so == 2 and swaps == 2
+        assert idx.cpu().numpy().tolist() == Io.tolist()
+        assert np.abs(B.cpu().numpy() - Bo).max() <= 1e-9 * max(1.0, np.abs(Bo).max())
+
+
 def test_maxvol_with_one_spare_row_finds_the_maximum_volume(W, H):
     rng = np.random.default_rng(2)
     mats = [rng.standard_normal((r + 1, r)) for r in (2, 3, 4, 5) for _ in range(5)]
