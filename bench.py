@@ -452,8 +452,7 @@ def bench_tt_cross(weno, I, torch, insts, reps=3, fd=0, sweeps=1):
     weno.weno_destroy(h)
     return {"workload": "tt_cross_x_residual_64_instances", "value": samples / (ms * 1e-3) / 1e6,
             "unit": "Msample/s", "ms_per_call": ms, "samples_per_call": samples, "sweeps": sweeps,
-            "kernels_ms_per_call": {"fiber_eval": kms[7] / reps, "qr": kms[0] / reps,
-                                    "maxvol_and_bookkeeping": kms[1] / reps},
+            "kernels_ms_per_call": {"fiber_eval": kms[7] / reps, "maxvol_and_bookkeeping": kms[1] / reps},
             "gpu_launches_per_call": launches / reps}
 
 

@@ -357,14 +357,16 @@ typedef struct {
     int32_t *idx;       /* device, r: receives the selected rows I */
 } weno_maxvol_problem;
 
-/* Batched maxvol, FP64, one thread-block cluster per matrix: the r pivot
- * rows of Gaussian elimination with partial pivoting, B = A A[I]^{-1}, then
- * row swaps while
- * some |B[i][j]| > 1 + delta (each swap multiplies |det A[I]| by |B[i][j]|;
- * ties go to the first entry in row-major order) or max_iters swaps are done.
- * probs: HOST array; synchronises the stream; swaps (host, may be NULL)
- * receives the swaps per matrix.  Errors: WENO_ERR_ARG for bad sizes, null
- * pointers, or a matrix whose pivot rows are singular (rank < r). */
+/* Batched maxvol (Sec. 3, "TT-cross Interpolation"), FP64, one thread-block
+ * cluster per matrix: the r pivot rows I of Gaussian elimination with partial
+ * pivoting (ties to the smaller row), B = A A[I]^{-1} formed from the
+ * elimination's multipliers L as L L[I]^{-1} (rows I exactly the unit
+ * vectors), then row swaps while some |B[i][j]| > 1 + delta (each swap
+ * multiplies |det A[I]| by |B[i][j]|; ties go to the first entry in row-major
+ * order) or max_iters swaps are done.  probs: HOST array, at most 65535
+ * matrices; synchronises the stream; swaps (host, may be NULL) receives the
+ * swaps per matrix.  Errors: WENO_ERR_ARG for bad sizes, null pointers, or a
+ * matrix whose elimination meets a zero pivot column (rank < r). */
 int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int32_t n_probs, double delta, int32_t max_iters,
                 int32_t *swaps);
 
@@ -384,8 +386,10 @@ typedef struct {
 /* Alternating TT-cross with maxvol index selection (Sec. 3, "TT-cross
  * Interpolation"; AMEn's rank adaptation is not part of it).  For every
  * instance i (problem i): a left-to-right pass evaluates A(:, J1), A(I1, :, J2),
- * A(I2, :, :) as fiber sets, takes the Householder Q of each unfolding and
- * maxvol's rows of Q to form I1, I2 and the interpolation cores Q Q[I]^{-1};
+ * A(I2, :, :) as fiber sets and takes maxvol's rows of each unfolding C to
+ * form I1, I2 and the interpolation cores C C[I]^{-1} (no orthogonalisation
+ * first: maxvol's pivots and C C[I]^{-1} depend only on C's column space, so
+ * they equal those of C's Householder Q);
  * `sweeps` times a right-to-left pass updates J2 and J1 the same way before the
  * next left-to-right pass.  The resulting TT interpolates A on the final index
  * sets.  Fibers are evaluated in FP32 (FP64 with WENO_CROSS_FP64_CHECK in

@@ -391,7 +391,7 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
                            int32_t max_iters, int32_t *swaps)
 {
     if (!h) return WENO_ERR_ARG;
-    if (!probs || n_probs < 1) return fail(h, WENO_ERR_ARG, "weno_maxvol: empty input");
+    if (!probs || n_probs < 1 || n_probs > 65535) return fail(h, WENO_ERR_ARG, "weno_maxvol: need 1..65535 matrices");
     if (!(delta >= 0.0) || max_iters < 0) return fail(h, WENO_ERR_ARG, "weno_maxvol: need delta >= 0, max_iters >= 0");
     std::vector<MaxvolDesc> ds(n_probs);
     size_t w_total = 0;
@@ -413,9 +413,9 @@ extern "C" int weno_maxvol(weno_handle h, const weno_maxvol_problem *probs, int3
     double *w = (double *)(base + off_w);
     for (int i = 0; i < n_probs; ++i) {
         const weno_maxvol_problem &P = probs[i];
-        double *minv = w + (((size_t)P.n * P.r + 31) & ~size_t(31));
-        ds[i] = MaxvolDesc{P.A, P.B, w, minv, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
-        w = minv + (((size_t)P.r * P.r + 31) & ~size_t(31));
+        double *linv = w + (((size_t)P.n * P.r + 31) & ~size_t(31));
+        ds[i] = MaxvolDesc{P.A, P.B, w, linv, P.idx, ints + 2 * i, ints + 2 * i + 1, P.n, P.r};
+        w = linv + (((size_t)P.r * P.r + 31) & ~size_t(31));
     }
     maxvol_order(ds.data(), n_probs);
     MaxvolDesc *dd = (MaxvolDesc *)(base + off_desc);
@@ -447,10 +447,8 @@ struct XProb {
     void *outL0 = nullptr, *outL1 = nullptr, *outL2 = nullptr;
     int *right0 = nullptr, *left1 = nullptr, *right1 = nullptr, *left2 = nullptr;
     double *M0 = nullptr, *M1 = nullptr, *MR2 = nullptr, *MR1 = nullptr;
-    double *Q0 = nullptr, *Q1 = nullptr, *QR2 = nullptr, *QR1 = nullptr;
-    double *B1 = nullptr, *BR = nullptr, *Wmv = nullptr, *Minv = nullptr;
+    double *B1 = nullptr, *BR = nullptr, *Wmv = nullptr, *Linv = nullptr;
     int *idx = nullptr;
-    QRPlan q0, q1, qr2, qr1;
 };
 }  // namespace
 
@@ -479,14 +477,10 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
         if (!P.J1 || !P.J2 || !P.I1 || !P.I2 || !P.core[0] || !P.core[1] || !P.core[2])
             return fail(h, WENO_ERR_ARG, "weno_tt_cross: null index set or core");
         max_r = std::max({max_r, x.r1, x.r2});
-        qr_plan(x.q0, n1, x.r1);
-        qr_plan(x.q1, (long long)x.r1 * n2, x.r2);
-        qr_plan(x.qr2, 5 * n3, x.r2);
-        qr_plan(x.qr1, n2 * x.r2, x.r1);
     }
     const int n_mv = 2 * (sweeps + 1) + 2 * sweeps;  // maxvol calls of the whole run
-    const int NSLOT = 6;
-    const size_t dsz = std::max({sizeof(QRDesc), sizeof(QApplyDesc), sizeof(MaxvolDesc), sizeof(CrossDrvDesc)});
+    const int NSLOT = 4;
+    const size_t dsz = std::max(sizeof(MaxvolDesc), sizeof(CrossDrvDesc));
     auto layout = [&](Bump &bp) -> char * {
         char *desc = bp.take<char>(dsz * NSLOT * 2 * (size_t)np);
         for (auto &x : xp) {
@@ -502,20 +496,12 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
             x.M1 = bp.take<double>(r1 * n2 * r2);
             x.MR2 = bp.take<double>(5 * n3 * r2);
             x.MR1 = bp.take<double>(n2 * r2 * r1);
-            x.Q0 = bp.take<double>(n1 * r1);
-            x.Q1 = bp.take<double>(r1 * n2 * r2);
-            x.QR2 = bp.take<double>(5 * n3 * r2);
-            x.QR1 = bp.take<double>(n2 * r2 * r1);
             x.B1 = bp.take<double>(r1 * n2 * r2);
             const size_t mk = std::max({n1 * r1, r1 * n2 * r2, 5 * n3 * r2, n2 * r2 * r1});
             x.BR = bp.take<double>(mk);
             x.Wmv = bp.take<double>(mk);
-            x.Minv = bp.take<double>(std::max(r1, r2) * std::max(r1, r2));
+            x.Linv = bp.take<double>(std::max(r1, r2) * std::max(r1, r2));
             x.idx = bp.take<int>(std::max(r1, r2));
-            qr_take(bp, x.q0);
-            qr_take(bp, x.q1);
-            qr_take(bp, x.qr2);
-            qr_take(bp, x.qr1);
         }
         return desc;
     };
@@ -570,35 +556,20 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
         return weno_cross_eval(h, inst, np, fs.data(), np, fp64 ? WENO_CROSS_FP64_CHECK : 0);
     };
     int mv_call = 0;
-    // QR (explicit Q) of every problem's matrix for this step, then maxvol on Q
-    auto select = [&](QRPlan XProb::*qp, double *XProb::*Mp, double *XProb::*Qp, double *XProb::*Bp,
-                      bool b_is_core0) -> int {
-        std::vector<QRPlan *> ps;
-        std::vector<ApplyReq> ar(np);
+    // maxvol on every problem's fiber matrix of this step (rows x cols); no
+    // orthogonalisation first: the pivot rows and B = M M[I]^{-1} depend only
+    // on M's column space, and B is formed from the elimination's multipliers
+    auto select = [&](double *XProb::*Mp, double *XProb::*Bp, bool b_is_core0, auto &&dims) -> int {
         std::vector<MaxvolDesc> md(np);
-        for (int i = 0; i < np; ++i) {
-            XProb &x = xp[i];
-            QRPlan &q = x.*qp;
-            q.A = x.*Mp;
-            ps.push_back(&q);
-        }
-        int rr = tt_factor(h, ps, (QRDesc *)slot(1));
-        if (rr) return rr;
-        for (int i = 0; i < np; ++i) {
-            XProb &x = xp[i];
-            QRPlan &q = x.*qp;
-            // explicit Q (m x k): apply to the identity, row-major; the chunk stack reuses W
-            ar[i] = ApplyReq{&q, nullptr, q.k, q.k, x.Wmv, x.*Qp, q.m, q.k, 0, 1};
-        }
-        if ((rr = tt_apply(h, ar, (QApplyDesc *)slot(2)))) return rr;
         int mr = 1;
         for (int i = 0; i < np; ++i) {
             XProb &x = xp[i];
-            QRPlan &q = x.*qp;
+            int rows, cols;
+            dims(x, rows, cols);
             double *Bout = b_is_core0 ? probs[i].core[0] : x.*Bp;
             int *st = status + 2 * ((size_t)mv_call * np + i);
-            md[i] = MaxvolDesc{x.*Qp, Bout, x.Wmv, x.Minv, x.idx, st, st + 1, (int)q.m, q.k};
-            mr = std::max(mr, q.k);
+            md[i] = MaxvolDesc{x.*Mp, Bout, x.Wmv, x.Linv, x.idx, st, st + 1, rows, cols};
+            mr = std::max(mr, cols);
         }
         maxvol_order(md.data(), np);
         MaxvolDesc *dd = (MaxvolDesc *)slot(3);
@@ -607,6 +578,10 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
         ++mv_call;
         return WENO_OK;
     };
+    auto dims_l0 = [](const XProb &x, int &m, int &k) { m = x.n[0]; k = x.r1; };
+    auto dims_l1 = [](const XProb &x, int &m, int &k) { m = x.r1 * x.n[1]; k = x.r2; };
+    auto dims_r2 = [](const XProb &x, int &m, int &k) { m = 5 * x.n[2]; k = x.r2; };
+    auto dims_r1 = [](const XProb &x, int &m, int &k) { m = x.n[1] * x.r2; k = x.r1; };
     auto nofill = [](XProb &, const weno_tt_cross_problem &, CrossDrvDesc &) {};
     for (int it = 0; it <= sweeps; ++it) {
         // ---- left to right
@@ -618,7 +593,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
                  c.M = x.M0;
              })))
             return r;
-        if ((r = select(&XProb::q0, &XProb::M0, &XProb::Q0, &XProb::BR, true))) return r;
+        if ((r = select(&XProb::M0, &XProb::BR, true, dims_l0))) return r;
         if ((r = drv(XD_UPDATE_L0, nofill))) return r;
         if ((r = drv(XD_PREP_L1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
                  c.left = x.left1;
@@ -631,7 +606,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
                  c.M = x.M1;
              })))
             return r;
-        if ((r = select(&XProb::q1, &XProb::M1, &XProb::Q1, &XProb::B1, false))) return r;
+        if ((r = select(&XProb::M1, &XProb::B1, false, dims_l1))) return r;
         if ((r = drv(XD_UPDATE_L1, [](XProb &x, const weno_tt_cross_problem &P, CrossDrvDesc &c) {
                  c.B = x.B1;
                  c.core = P.core[1];
@@ -648,7 +623,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
             return r;
         if (it == sweeps) break;
         // ---- right to left
-        if ((r = select(&XProb::qr2, &XProb::MR2, &XProb::QR2, &XProb::BR, false))) return r;
+        if ((r = select(&XProb::MR2, &XProb::BR, false, dims_r2))) return r;
         if ((r = drv(XD_UPDATE_R2, nofill))) return r;
         if ((r = drv(XD_PREP_L1, [](XProb &x, const weno_tt_cross_problem &, CrossDrvDesc &c) {
                  c.left = x.left1;
@@ -661,7 +636,7 @@ extern "C" int weno_tt_cross(weno_handle h, const weno_tt_instance *inst, int32_
                  c.M = x.MR1;
              })))
             return r;
-        if ((r = select(&XProb::qr1, &XProb::MR1, &XProb::QR1, &XProb::BR, false))) return r;
+        if ((r = select(&XProb::MR1, &XProb::BR, false, dims_r1))) return r;
         if ((r = drv(XD_UPDATE_R1, nofill))) return r;
     }
     std::vector<int> st(2 * (size_t)n_mv * np);

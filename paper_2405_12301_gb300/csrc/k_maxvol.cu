@@ -1,23 +1,27 @@
 // k_maxvol.cu -- batched maxvol (the maximum-volume row selection that picks
 // the cross indices of TT-cross, Sec. 3 "TT-cross Interpolation"), FP64, three
 // launches per batch:
-//   1. the r pivot rows of Gaussian elimination with partial pivoting on a
+//   1. the r pivot rows I of Gaussian elimination with partial pivoting on a
 //      working copy W (largest remaining |W[i][j]| of column j, ties to the
-//      smaller row), then A[I]^{-1} by Gauss-Jordan with partial pivoting;
-//   2. B = A A[I]^{-1}, spread over many CTAs per matrix;
+//      smaller row); the multipliers L[i][j] overwrite column j of W, and the
+//      unit lower triangular L[I] is inverted;
+//   2. B = A A[I]^{-1} = L L[I]^{-1} (A = P L U, so the U factor cancels; the
+//      rows I get the unit vectors exactly), spread over many CTAs per matrix;
 //   3. while max |B[i][j]| > 1 + delta (ties to the first entry in row-major
 //      order): row i replaces I[j] and B -= B[:, j] (B[i, :] - e_j) / B[i][j].
-// Phases 1 and 3 are sequences of (argmax, rank-one update) steps.  Each matrix
-// gets a thread-block cluster whose CTAs own contiguous slices of its rows, so
-// the FP64 work of a large matrix spreads over up to 16 SMs.  Per step every
-// CTA finds the best entry of its slice and stashes that entry's row in a
-// shared-memory slot; after one cluster barrier every CTA reduces the slots
-// (read through distributed shared memory) to the same winner and copies the
-// winner's row from its owner.  Slots alternate between two buffers, so the
-// writes of step t + 1 never meet the reads of step t, and the stash lets the
-// owner update the winning row in place while others still read it.  The
-// working copy is column-major (W[c][i]), so a warp's row-parallel accesses
-// coalesce; it stays in L2.
+// Forming B from L rather than from an inverse of A[I] keeps it accurate when
+// A is ill-conditioned: |L| <= 1 under partial pivoting, and the scale of
+// A's columns stays in U.  Phases 1 and 3 are sequences of (argmax, rank-one
+// update) steps.  Each matrix gets a thread-block cluster whose CTAs own
+// contiguous slices of its rows, so the FP64 work of a large matrix spreads
+// over up to 16 SMs.  Per step every CTA finds the best entry of its slice and
+// stashes that entry's row in a shared-memory slot; after one cluster barrier
+// every CTA reduces the slots (read through distributed shared memory) to the
+// same winner and copies the winner's row from its owner.  Slots alternate
+// between two buffers, so the writes of step t + 1 never meet the reads of
+// step t, and the stash lets the owner update the winning row in place while
+// others still read it.  The working copy is column-major (W[c][i]), so a
+// warp's row-parallel accesses coalesce; it stays in L2.
 #include <algorithm>
 #include <climits>
 
@@ -32,6 +36,11 @@ namespace wg {
 namespace cg = cooperative_groups;
 
 constexpr int MV_NT = 256, MV_NW = MV_NT / 32;
+// A pivot |w| <= MV_RANK_TOL r max_i |A[i][j]| counts as zero: the residual
+// of a column that lies in the span of the earlier ones is a few rounding
+// errors of the column's own scale (a full-rank matrix reaches it only with a
+// condition number near 1 / (r MV_RANK_TOL) ~ 1e13).
+constexpr double MV_RANK_TOL = 4.0 * 2.220446049250313e-16;
 
 // |x| as an unsigned integer: for finite x its order is the order of |x|, so
 // argmaxes run on the integer pipe (FP64 compares issue at the FP64 rate).
@@ -146,10 +155,10 @@ __device__ __forceinline__ void row_slice(int n, int rank, int ncl, int &lo, int
     hi = (int)((long long)(rank + 1) * n / ncl);
 }
 
-size_t maxvol_smem(int r) { return sizeof(double) * (size_t)r * (2 * r + 1); }
+size_t maxvol_smem(int r) { return sizeof(double) * (size_t)r * 2 * r; }
 
-// Phase 1: pivot rows (the whole cluster), then the Gauss-Jordan inverse of
-// A[I] (rank 0 alone, in dynamic shared memory).
+// Phase 1: pivot rows and multipliers (the whole cluster), then L[I]^{-1}
+// (rank 0 alone, in dynamic shared memory).
 __global__ void __launch_bounds__(MV_NT) k_maxvol_pivot(const MaxvolDesc *descs)
 {
     cg::cluster_group cl = cg::this_cluster();
@@ -161,10 +170,30 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol_pivot(const MaxvolDesc *descs)
     __shared__ int I[MV_RMAX];
     __shared__ unsigned chosen[MV_NMAX / 8 / 32];  // rows of this slice already picked (slices have <= n/8 + 1 rows)
     __shared__ int s_fail;
+    __shared__ unsigned long long cbits[MV_RMAX];  // this CTA's column maxima of |A| (bit patterns)
+    __shared__ double ctol[MV_RMAX];
     double *W = d.W;
+    if (threadIdx.x == 0) s_fail = 0;
     for (int e = threadIdx.x; e < (hi - lo + 31) / 32; e += MV_NT) chosen[e] = 0u;
     for (int i = lo + threadIdx.x; i < hi; i += MV_NT)  // column-major copy; a thread reads its row in order
         for (int c = 0; c < r; ++c) W[(long long)c * n + i] = d.A[(long long)i * r + c];
+    // the scale of every column, max_i |A[i][c]|, over the whole cluster: a
+    // pivot at or below MV_RANK_TOL of its column's scale means rank < r
+    for (int c = threadIdx.x; c < r; c += MV_NT) cbits[c] = 0ull;
+    __syncthreads();
+    for (int c = 0; c < r; ++c) {
+        unsigned long long m = 0ull;
+        for (int i = lo + threadIdx.x; i < hi; i += MV_NT) m = max(m, absbits(W[(long long)c * n + i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if ((threadIdx.x & 31) == 0 && m) atomicMax(&cbits[c], m);
+    }
+    cl.sync();
+    for (int c = threadIdx.x; c < r; c += MV_NT) {
+        unsigned long long m = 0ull;
+        for (int q = 0; q < ncl; ++q) m = max(m, *cl.map_shared_rank(&cbits[c], q));
+        ctol[c] = MV_RANK_TOL * r * __longlong_as_double((long long)m);
+    }
     __syncthreads();
 
     // 1. partial pivoting; only the columns after j are updated (earlier ones
@@ -193,11 +222,15 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol_pivot(const MaxvolDesc *descs)
         }
         __syncthreads();
         const double wp = st.row[j];
-        if (wp != 0.0 && j + 1 < r) {
+        if (!(fabs(wp) > ctol[j])) {
+            if (threadIdx.x == 0) s_fail = 1;  // every CTA sees the same pivot and scale
+        } else {
             const double inv = 1.0 / wp;
             for (int i = lo + threadIdx.x; i < hi; i += MV_NT) {
                 if ((chosen[(i - lo) >> 5] >> ((i - lo) & 31)) & 1u) continue;
-                const double f = W[(long long)j * n + i] * inv;
+                double *wj = W + (long long)j * n + i;
+                const double f = *wj * inv;
+                *wj = f;  // L[i][j]
                 for (int c = j + 1; c < r; ++c) {
                     double *w = W + (long long)c * n + i;
                     *w = fma(-f, st.row[c], *w);
@@ -210,77 +243,60 @@ __global__ void __launch_bounds__(MV_NT) k_maxvol_pivot(const MaxvolDesc *descs)
     cl.sync();  // no CTA leaves while another may still read its slots
     if (rank != 0) return;
 
-    // A[I]^{-1}: Gauss-Jordan on [A[I] | identity], pivot search on the
-    // integer pipe, row swap, scaling and elimination spread over the block
-    extern __shared__ double G[];  // [r][2r]
-    const int r2 = 2 * r;
-    for (int e = threadIdx.x; e < r * r2; e += MV_NT) {
-        const int i = e / r2, c = e - i * r2;
-        G[e] = c < r ? d.A[(long long)I[i] * r + c] : (c - r == i ? 1.0 : 0.0);
+    // L[I]^{-1}: L[I] is unit lower triangular, row k holding the multipliers
+    // of row I[k] from the steps before k (other slices' rows are read from L2:
+    // they were written before the barrier above)
+    extern __shared__ double G[];
+    double *Lt = G;                       // [r][r]
+    double *Li = G + (size_t)r * r;       // [r][r]
+    for (int e = threadIdx.x; e < r * r; e += MV_NT) {
+        const int k = e / r, m = e - k * r;
+        Lt[e] = m < k ? __ldcg(W + (long long)m * n + I[k]) : (m == k ? 1.0 : 0.0);
     }
-    if (threadIdx.x == 0) s_fail = 0;
-    __shared__ int s_piv;
     __syncthreads();
-    for (int c = 0; c < r; ++c) {
-        if (threadIdx.x == 0) {
-            int p = c;
-            unsigned long long best = absbits(G[c * r2 + c]);
-            for (int i = c + 1; i < r; ++i) {
-                const unsigned long long k = absbits(G[i * r2 + c]);
-                if (k > best) {
-                    best = k;
-                    p = i;
-                }
-            }
-            if (best == 0ull) s_fail = 1;
-            s_piv = p;
+    // column c of the inverse by forward substitution, one thread per column
+    for (int c = threadIdx.x; c < r; c += MV_NT) {
+        for (int k = 0; k < c; ++k) Li[k * r + c] = 0.0;
+        Li[c * r + c] = 1.0;
+        for (int k = c + 1; k < r; ++k) {
+            double acc = 0.0;
+            for (int m = c; m < k; ++m) acc = fma(Lt[k * r + m], Li[m * r + c], acc);
+            Li[k * r + c] = -acc;
         }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != c)
-            for (int t = c + threadIdx.x; t < r2; t += MV_NT) {
-                const double x = G[c * r2 + t];
-                G[c * r2 + t] = G[p * r2 + t];
-                G[p * r2 + t] = x;
-            }
-        __syncthreads();
-        const double gcc = G[c * r2 + c];
-        const double inv = gcc == 0.0 ? 0.0 : 1.0 / gcc;
-        __syncthreads();
-        for (int t = c + threadIdx.x; t < r2; t += MV_NT) G[c * r2 + t] *= inv;
-        __syncthreads();
-        for (int i = threadIdx.x; i < r; i += MV_NT) st.row[i] = G[i * r2 + c];  // multipliers, read before any write
-        __syncthreads();
-        const int w = r2 - c;  // columns c..2r-1 (the ones before c are already unit vectors)
-        for (int e = threadIdx.x; e < r * w; e += MV_NT) {
-            const int i = e / w, t = c + (e - i * w);
-            if (i == c) continue;
-            G[i * r2 + t] = fma(-st.row[i], G[c * r2 + t], G[i * r2 + t]);
-        }
-        __syncthreads();
     }
+    __syncthreads();
     if (threadIdx.x == 0) d.status[0] = s_fail;
     if (s_fail) return;
-    for (int e = threadIdx.x; e < r * r; e += MV_NT) {
-        const int k = e / r, c = e - k * r;
-        d.Minv[e] = G[k * r2 + r + c];
-    }
+    for (int e = threadIdx.x; e < r * r; e += MV_NT) d.Linv[e] = Li[e];
     for (int j = threadIdx.x; j < r; j += MV_NT) d.idx[j] = I[j];
 }
 
-// B = A A[I]^{-1}: the n x r by r x r product, spread over many CTAs per matrix.
-__global__ void k_maxvol_b(const MaxvolDesc *descs)
+// B = L L[I]^{-1} (L: the multipliers in W, column-major), spread over many
+// CTAs per matrix; the pivot rows get the unit vectors.
+__global__ void __launch_bounds__(256) k_maxvol_b(const MaxvolDesc *descs)
 {
     const MaxvolDesc &d = descs[blockIdx.y];
     if (d.status[0]) return;
-    const int r = d.r;
-    const long long nr = (long long)d.n * r;
+    const int n = d.n, r = d.r;
+    __shared__ double Li[MV_RMAX * MV_RMAX];
+    __shared__ unsigned piv[MV_NMAX / 32];  // rows in I
+    __shared__ int I[MV_RMAX];
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Li[e] = d.Linv[e];
+    for (int w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) piv[w] = 0u;
+    for (int k = threadIdx.x; k < r; k += blockDim.x) I[k] = d.idx[k];
+    __syncthreads();
+    for (int k = threadIdx.x; k < r; k += blockDim.x) atomicOr(&piv[I[k] >> 5], 1u << (I[k] & 31));
+    __syncthreads();
+    const double *W = d.W;
+    const long long nr = (long long)n * r;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / r;
-        const int c = (int)(e - i * r);
-        const double *ai = d.A + i * r;
+        const int i = (int)(e / r), c = (int)(e - (long long)i * r);
         double acc = 0.0;
-        for (int k = 0; k < r; ++k) acc = fma(ai[k], d.Minv[k * r + c], acc);
+        if ((piv[i >> 5] >> (i & 31)) & 1u) {
+            acc = I[c] == i ? 1.0 : 0.0;
+        } else {
+            for (int k = c; k < r; ++k) acc = fma(W[(long long)k * n + i], Li[k * r + c], acc);
+        }
         d.B[e] = acc;
     }
 }

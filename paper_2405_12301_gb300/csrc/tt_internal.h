@@ -93,8 +93,8 @@ constexpr int MV_NMAX = 1 << 16;  // rows of a maxvol matrix
 struct MaxvolDesc {
     const double *A;   // n x r row-major
     double *B;         // n x r: A A[I]^{-1} on exit
-    double *W;         // n x r scratch
-    double *Minv;      // r x r scratch: A[I]^{-1} of the pivot rows
+    double *W;         // n x r scratch (column-major working copy, then the multipliers L)
+    double *Linv;      // r x r scratch: the inverse of the unit lower triangular L[I]
     int *idx;          // r selected rows
     int *status;       // 0 ok, 1 A[I] singular after pivoting
     int *swaps;

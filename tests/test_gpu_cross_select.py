@@ -81,6 +81,24 @@ def test_maxvol_stops_at_max_iters(W, H):
         assert np.abs(B.cpu().numpy() - Bo).max() <= 1e-9 * max(1.0, np.abs(Bo).max())
 
 
+def test_maxvol_of_an_ill_conditioned_matrix_equals_that_of_its_q_factor(W, H):
+    """maxvol's pivots and B = A A[I]^{-1} depend only on A's column space when
+    A = Q R with R upper triangular (the Schur-complement residual of Q's column
+    j is a multiple of A's), which is why the TT-cross path skips the QR: the
+    GPU's rows for A equal the oracle's rows for Q, and B agrees to about
+    eps cond(A)."""
+    rng = np.random.default_rng(7)
+    for n, r, c, tol in [(3000, 32, 1e-4, 1e-8), (500, 12, 1e-8, None)]:
+        G = rng.standard_normal((n, r)) * np.geomspace(1, c, r)
+        A = G @ (np.eye(r) + 0.5 * np.triu(rng.standard_normal((r, r)), 1))
+        (idx, B, swaps), = W.weno_maxvol(H, [torch.from_numpy(A).cuda()], delta=1e-2)
+        Io, Bo, so = X.maxvol(np.linalg.qr(A)[0], delta=1e-2)
+        assert idx.cpu().numpy().tolist() == Io.tolist()
+        assert swaps == so
+        if tol is not None:
+            assert np.abs(B.cpu().numpy() - Bo).max() <= tol
+
+
 def test_maxvol_with_one_spare_row_finds_the_maximum_volume(W, H):
     rng = np.random.default_rng(2)
     mats = [rng.standard_normal((r + 1, r)) for r in (2, 3, 4, 5) for _ in range(5)]
