@@ -57,8 +57,10 @@ template <int D, bool BULK> struct Layout {
 };
 }  // namespace xy
 
+// The 2D FP32-bulk kernel is held to 48 registers so that 5 CTAs (40 warps)
+// share an SM; its shared memory (42.5 KB) allows that many.
 template <int D, bool BULK, int EPI, bool PD>
-__global__ void __launch_bounds__(xy::NT) k_xy(const SweepArgs a)
+__global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const SweepArgs a)
 {
     using namespace xy;
     using L = Layout<D, BULK>;
