@@ -34,6 +34,9 @@ constexpr int BXP = BX + 3;                 // row pitch of the x-flux points (4
                                             // runs of phase W read 8 rows x 4 components per
                                             // warp without bank conflicts)
 constexpr int NXP = BXP * TY;               // x-flux points: 38 (pitch 41) x 8
+constexpr int BXP2 = BX + 1;                // the same in float2 pairs (39: any odd pitch lets a
+                                            // warp's 8 rows x 4 segments of 64-bit reads hit
+                                            // distinct banks)
 constexpr int NYP = TX * BY;                // y-flux points: 32 x 14
 constexpr int NXI = (TX + 1) * TY;          // x interfaces: 33 x 8
 constexpr int NYI = TX * (TY + 1);          // y interfaces: 32 x 9
@@ -45,13 +48,18 @@ constexpr int NHALO = NHY + 6 * TY;         // plus x-halo points: 240
 // components) one thread per cell.
 template <int D> constexpr bool slide() { return D == 2; }
 
+// PK: the 2D FP32-bulk kernel keeps the four components as two float2 pairs,
+// (rho, m_x) and (m_y, E), in its flux and face arrays and reconstructs a pair
+// per sliding run with f32x2 arithmetic (half the issue slots of scalar FP32).
 template <int D, bool BULK> struct Layout {
     using T = typename std::conditional<BULK, float, double>::type;
     static constexpr int NF = D + 2;
+    static constexpr bool PK = D == 2 && BULK;
     static constexpr int NS = slide<D>() ? 2 : 1;                             // face-flux copies
+    static constexpr int NXPC = PK ? BXP2 * TY : NXP;                         // x-flux points per component
     static constexpr size_t F_off = 0;                                        // Fx, Fy
     static constexpr size_t fx_off = (sizeof(T) * NS * NF * (NXI + NYI) + 15) & ~size_t(15);
-    static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXP;
+    static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXPC;
     static constexpr size_t ref_off = (fy_off + sizeof(T) * 2 * NF * NYP + 15) & ~size_t(15);
     static constexpr size_t bytes = ref_off + sizeof(RefState<D>);
 };
@@ -72,6 +80,11 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
     T *fx = reinterpret_cast<T *>(smem + L::fx_off);       // [2][NF][TY][BXP]
     T *fy = reinterpret_cast<T *>(smem + L::fy_off);       // [2][NF][BY][TX]
     RefState<D> &ref = *reinterpret_cast<RefState<D> *>(smem + L::ref_off);
+    // PK views: [sign][pair] blocks of float2 (Fx2 [2][2][TY][TX+1], Fy2 [2][2][TY+1][TX],
+    // fx2 [2][2][TY][BXP2], fy2 [2][2][BY][TX])
+    float2 *Fx2 = reinterpret_cast<float2 *>(Fx), *Fy2 = reinterpret_cast<float2 *>(Fy);
+    float2 *fx2 = reinterpret_cast<float2 *>(fx), *fy2 = reinterpret_cast<float2 *>(fy);
+    constexpr int NXP2 = BXP2 * TY;
 
     // dt and alpha come from the control block; the FP32 path converts them on
     // the integer pipe (a cvt issues at FP64 rate on this GPU)
@@ -93,8 +106,10 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
     const long long cell = zoff + (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
 
     // the stage combination needs U^n at this thread's cell: issue the loads now
+    // (the packed kernel loads it after phase W instead, and re-reads U^k and
+    // re-splits it there: holding them through the reconstruction would spill)
     double un[NF];
-    if (EPI == EPI_STAGE && a.stage > 0) {
+    if (EPI == EPI_STAGE && a.stage > 0 && !L::PK) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
@@ -150,7 +165,14 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
             if (dirx) split_flux_f64<D, 0, true>(q, alX, gm1, fp, fm);
             else split_flux_f64<D, 1, true>(q, alY, gm1, fp, fm);
         }
-        if (dirx) {
+        if constexpr (L::PK) {
+            float2 *b = dirx ? fx2 + ly * BXP2 + (lx + 3) : fy2 + (ly + 3) * TX + lx;
+            const int np = dirx ? NXP2 : NYP;
+            b[0] = make_float2(fp[0], fp[1]);
+            b[np] = make_float2(fp[2], fp[3]);
+            b[2 * np] = make_float2(fm[0], fm[1]);
+            b[3 * np] = make_float2(fm[2], fm[3]);
+        } else if (dirx) {
             const int o = ly * BXP + (lx + 3);
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -230,7 +252,36 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
                weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
     };
     T fxl[NF], fyb[NF];
-    if constexpr (slide<D>()) {
+    if constexpr (L::PK) {
+        // One packed run of TY + 1 = 9 windows per thread (pair w & 1, sign (w >> 1) & 1):
+        //   warps 0-3, y: column `lane`, faces 0..8;
+        //   warps 4-7, x: row lane & 7, faces 8 s .. 8 s + 8 for s = lane >> 3 --
+        //      neighbouring segments share one face and write it with the same value.
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
+        const int blk = sg * 2 + pr;
+        const float2 *p;
+        float2 *out;
+        int st, os;
+        if (w < 4) {
+            p = fy2 + blk * NYP + lane;
+            out = Fy2 + blk * NYI + lane;
+            st = TX;
+            os = TX;
+        } else {
+            const int ly = lane & 7, j0 = (lane >> 3) * 8;
+            p = fx2 + blk * NXP2 + ly * BXP2 + j0;
+            out = Fx2 + blk * NXI + ly * (TX + 1) + j0;
+            st = 1;
+            os = 1;
+        }
+        if (sg) {  // WENO(-): the same run read backwards from the far end
+            p += (TY + 5) * st;
+            out += TY * os;
+            st = -st;
+            os = -os;
+        }
+        weno5_slide2<TY + 1>(p, st, (float)eps, out, os);
+    } else if constexpr (slide<D>()) {
         // Two runs of TY + 1 = 9 windows per thread, one code path (a single
         // unrolled copy keeps the kernel inside the instruction cache):
         //   y: column `lane`, component w & 3, sign w >> 2, faces 0..8;
@@ -286,13 +337,38 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
     }
     __syncthreads();
 
+    if constexpr (L::PK && EPI == EPI_STAGE) {  // U^n and U^k at the own cell (see above)
+        if (a.stage > 0) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            uk[f] = __ldg(a.U + f * N + cell);
+            split_f64(uk[f], hk[f], lk[f]);  // integer pipe; cheaper than holding them through phase W
+        }
+    }
+
     // ---- phase C: the cell's residual -(dF/dx) - (dG/dy) and the epilogue
     // face fluxes are twice F^: the halving rides on 1/h
     const T ihx = T(0.5) * (BULK ? (T)a.inv_h_f[0] : (T)a.inv_h[0]);
     const T ihy = T(0.5) * (BULK ? (T)a.inv_h_f[1] : (T)a.inv_h[1]);
     T r[NF];
+    if constexpr (L::PK) {
+        const float2 nihx = bc2(-(float)ihx), nihy = bc2(-(float)ihy);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+        for (int pr = 0; pr < 2; ++pr) {  // F^ = WENO(+) + WENO(-), both signs' blocks
+            const int ox = pr * NXI + ty * (TX + 1) + tx, oy = pr * NYI + ty * TX + tx;
+            const float2 *FxM = Fx2 + 2 * NXI, *FyM = Fy2 + 2 * NYI;
+            const float2 dx = sub2(add2(Fx2[ox + 1], FxM[ox + 1]), add2(Fx2[ox], FxM[ox]));
+            const float2 dy = sub2(add2(Fy2[oy + TX], FyM[oy + TX]), add2(Fy2[oy], FyM[oy]));
+            const float2 rr = fma2(dy, nihy, mul2(dx, nihx));
+            r[2 * pr] = rr.x;
+            r[2 * pr + 1] = rr.y;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < (L::PK ? 0 : NF); ++f) {
         T dx, dy;
         if constexpr (slide<D>()) {  // F^ = WENO(+) + WENO(-) at the right/top and left/bottom faces
             const int ox = f * NXI + ty * (TX + 1) + tx, oy = f * NYI + ty * TX + tx;
@@ -332,7 +408,9 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
         bool bad = false;
         if (own) {
             const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            // the packed kernel re-reads dt rather than holding it through phase W
+            const double dte = L::PK ? a.ctl->dt : dt;
+            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dte);
             float qn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {

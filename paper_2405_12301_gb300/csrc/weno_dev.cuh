@@ -215,6 +215,68 @@ __device__ __forceinline__ void weno5_slide(const T *p, int s, T eps, T *out, in
     }
 }
 
+// ------------------------------------------------- packed FP32 pairs (f32x2)
+// Two independent FP32 streams in one float2: a .f32x2 instruction takes one
+// issue slot for both operations (the FMA pipe still does two), which is what
+// an issue-bound kernel needs.  Each lane of a pair is rounded exactly as the
+// scalar operation would round it.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+    return *reinterpret_cast<const float2 *>(&r);
+}
+
+// weno5_slide for two streams at once (two components of the same line and
+// sign, stored as float2 pairs): the same operations in the same order on each
+// lane.  beta_2's (3 D2 - D1) enters only squared, so its negation D1 - 3 D2 is
+// formed instead (one FMA, and (q s) s is unchanged by the sign).
+template <int K>
+__device__ __forceinline__ void weno5_slide2(const float2 *p, int s, float eps_, float2 *out, int os)
+{
+    const float2 k13 = bc2((float)(13.0 / 12.0)), q = bc2(0.25f), eps = bc2(eps_);
+    const float2 v0 = *p, v1 = *(p += s);
+    float2 c = *(p += s), d = *(p += s);
+    float2 D1 = sub2(v1, v0), D2 = sub2(c, v1), D3 = sub2(d, c);
+    float2 t1 = sub2(D3, D2), t2 = sub2(D2, D1);
+    float2 A1 = fma2(mul2(k13, t1), t1, eps), A2 = fma2(mul2(k13, t2), t2, eps);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        const float2 e = *(p += s);
+        const float2 D4 = sub2(e, d);
+        const float2 t0 = sub2(D4, D3);
+        const float2 A0 = fma2(mul2(k13, t0), t0, eps);
+        const float2 s0 = fma2(bc2(-3.0f), D3, D4), s1 = add2(D2, D3), s2 = fma2(bc2(-3.0f), D2, D1);
+        float2 g0 = fma2(mul2(q, s0), s0, A0), g1 = fma2(mul2(q, s1), s1, A1), g2 = fma2(mul2(q, s2), s2, A2);
+        g0 = mul2(g0, g0);
+        g1 = mul2(g1, g1);
+        g2 = mul2(g2, g2);
+        const float2 w0 = mul2(bc2(0.3f), mul2(g1, g2)), w1 = mul2(bc2(0.6f), mul2(g0, g2)),
+                     w2 = mul2(bc2(0.1f), mul2(g0, g1));
+        const float2 sw = add2(add2(w0, w1), w2);
+        const float2 num =
+            fma2(w0, sub2(t1, t0), fma2(mul2(bc2(-2.0f), w2), sub2(t1, t2), mul2(fma2(bc2(2.0f), D3, D2), sw)));
+        const float2 den = mul2(bc2(6.0f), sw);
+        *out = fma2(num, make_float2(fast_rcp(den.x), fast_rcp(den.y)), c);
+        out += os;
+        D1 = D2;
+        D2 = D3;
+        D3 = D4;
+        t2 = t1;
+        t1 = t0;
+        A2 = A1;
+        A1 = A0;
+        c = d;
+        d = e;
+    }
+}
+
 // ----------------------------------------------------------- point fluxes
 
 // Plain FP64 Euler flux in direction DIR (Sec. 2.1) and its LF split
