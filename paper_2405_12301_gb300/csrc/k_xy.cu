@@ -65,10 +65,10 @@ template <int D, bool BULK> struct Layout {
 };
 }  // namespace xy
 
-// The 2D FP32-bulk kernel is held to 48 registers so that 5 CTAs (40 warps)
-// share an SM; its shared memory (42.5 KB) allows that many.
+// The FP32-bulk kernels are held to 48 registers so that 5 CTAs (40 warps)
+// share an SM; their shared memory (about 42 KB) allows that many.
 template <int D, bool BULK, int EPI, bool PD>
-__global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const SweepArgs a)
+__global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 {
     using namespace xy;
     using L = Layout<D, BULK>;
@@ -113,23 +113,11 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
-
-    // ---- reference state of the tile (FP32-bulk): its first cell
-    if (BULK) {
-        if (threadIdx.x < 32) {
-            const long long c0 = zoff + (long long)(y0 < ny ? y0 : ny - 1) * nx + (x0 < nx ? x0 : nx - 1);
-            double q[NF];
+    if (EPI == EPI_STAGE && a.stage > 0 && L::PK) {  // bring U^n into L2 for the late read
 #pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
-            RefState<D> r;
-            make_ref<D>(q, a.gm1_f, r);
-            if (threadIdx.x == 0) ref = r;
-        }
-        __syncthreads();
+        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Un + f * N + cell));
     }
-    const T alX = BULK ? (T)f64_to_f32(alx) : (T)alx;
-    const T alY = !PD ? alX : (BULK ? (T)f64_to_f32(aly) : (T)aly);
-    const double gm1 = a.gamma - 1.0;
+
     // interior tiles (halo inside the grid) skip the boundary rule
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
 
@@ -155,6 +143,50 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
         if (fx_) q[1] = -q[1];
         if (fy_) q[2] = -q[2];
     };
+
+    // ---- phase A+F: own point (x and y fluxes) and one halo point per thread;
+    // their loads go out before the reference state's barrier, so their latency
+    // overlaps warp 0's work on the reference
+    double uk[NF];                // U^(k) at the own cell, kept for the stage combination
+    float hk[NF], lk[NF];         // its hi/lo split (FP32-bulk)
+    load_point(tx, ty, uk);
+    const bool halo = threadIdx.x < NHALO;
+    int hx = 0, hy = 0;
+    bool hdirx = false;
+    double qd[NF];
+    if (halo) {
+        int t = threadIdx.x;
+        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
+            hx = t & 31;
+            const int k = t >> 5;
+            hy = k < 3 ? k - 3 : TY + k - 3;
+        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
+            t -= NHY;
+            hy = t / 6;
+            const int k = t - hy * 6;
+            hx = k < 3 ? k - 3 : TX + k - 3;
+            hdirx = true;
+        }
+        load_point(hx, hy, qd);
+    }
+
+    // ---- reference state of the tile (FP32-bulk): its first cell
+    if (BULK) {
+        if (threadIdx.x < 32) {
+            const long long c0 = zoff + (long long)(y0 < ny ? y0 : ny - 1) * nx + (x0 < nx ? x0 : nx - 1);
+            double q[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
+            RefState<D> r;
+            make_ref<D>(q, a.gm1_f, r);
+            if (threadIdx.x == 0) ref = r;
+        }
+        __syncthreads();
+    }
+    const T alX = BULK ? (T)f64_to_f32(alx) : (T)alx;
+    const T alY = !PD ? alX : (BULK ? (T)f64_to_f32(aly) : (T)aly);
+    const double gm1 = a.gamma - 1.0;
+
     // split flux of a point in direction DIR, stored at its slot of fx / fy
     auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
         T fp[NF], fm[NF];
@@ -189,10 +221,6 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
         }
     };
 
-    // ---- phase A+F: own point (x and y fluxes) and one halo point per thread
-    double uk[NF];                // U^(k) at the own cell, kept for the stage combination
-    float hk[NF], lk[NF];         // its hi/lo split (FP32-bulk)
-    load_point(tx, ty, uk);
     {
         T q[NF];
         if constexpr (BULK) {
@@ -208,30 +236,14 @@ __global__ void __launch_bounds__(xy::NT, (D == 2 && BULK) ? 5 : 1) k_xy(const S
         flux_store(q, true, tx, ty);
         flux_store(q, false, tx, ty);
     }
-    if (threadIdx.x < NHALO) {
-        int t = threadIdx.x, lx, ly;
-        bool dirx;
-        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
-            lx = t & 31;
-            const int k = t >> 5;
-            ly = k < 3 ? k - 3 : TY + k - 3;
-            dirx = false;
-        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
-            t -= NHY;
-            ly = t / 6;
-            const int k = t - ly * 6;
-            lx = k < 3 ? k - 3 : TX + k - 3;
-            dirx = true;
-        }
-        double qd[NF];
-        load_point(lx, ly, qd);
+    if (halo) {
         T q[NF];
         if constexpr (BULK) diff_from_ref<D>(qd, ref, q);
         else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = qd[f];
         }
-        flux_store(q, dirx, lx, ly);
+        flux_store(q, hdirx, hx, hy);
     }
     __syncthreads();
 
