@@ -251,17 +251,28 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     // one of the remaining faces (top of the tile's top row, right of its last column)
     // the shared arrays hold 2 f(+/-): reconstruct with 4 eps (twice the WENO5 value)
     const T eps = T(4) * (BULK ? (T)a.eps_f : (T)a.eps);
+    // (FP32: WENO(+) and the mirrored WENO(-) of a face as one f32x2 pair)
     auto face_x = [&](int f, int ly, int j) -> T {  // between local columns j-1 and j of row ly
         const T *P = fx + f * NXP + ly * BXP;
         const T *M = fx + (NF + f) * NXP + ly * BXP;
-        return weno5<T>(P[j], P[j + 1], P[j + 2], P[j + 3], P[j + 4], eps) +
-               weno5<T>(M[j + 5], M[j + 4], M[j + 3], M[j + 2], M[j + 1], eps);
+        if constexpr (BULK)
+            return weno5_pm(make_float2(P[j], M[j + 5]), make_float2(P[j + 1], M[j + 4]),
+                            make_float2(P[j + 2], M[j + 3]), make_float2(P[j + 3], M[j + 2]),
+                            make_float2(P[j + 4], M[j + 1]), eps);
+        else
+            return weno5<T>(P[j], P[j + 1], P[j + 2], P[j + 3], P[j + 4], eps) +
+                   weno5<T>(M[j + 5], M[j + 4], M[j + 3], M[j + 2], M[j + 1], eps);
     };
     auto face_y = [&](int f, int lx, int j) -> T {  // between local rows j-1 and j of column lx
         const T *P = fy + f * NYP + lx;
         const T *M = fy + (NF + f) * NYP + lx;
-        return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
-               weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
+        if constexpr (BULK)
+            return weno5_pm(make_float2(P[j * TX], M[(j + 5) * TX]), make_float2(P[(j + 1) * TX], M[(j + 4) * TX]),
+                            make_float2(P[(j + 2) * TX], M[(j + 3) * TX]), make_float2(P[(j + 3) * TX], M[(j + 2) * TX]),
+                            make_float2(P[(j + 4) * TX], M[(j + 1) * TX]), eps);
+        else
+            return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
+                   weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
     };
     T fxl[NF], fyb[NF];
     if constexpr (L::PK) {

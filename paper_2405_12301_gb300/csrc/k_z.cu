@@ -146,11 +146,17 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
 
     // the shared arrays hold 2 f(+/-): reconstruct with 4 eps (twice the WENO5 value)
     const T eps = T(4) * (BULK ? (T)a.eps_f : (T)a.eps);
+    // (FP32: WENO(+) and the mirrored WENO(-) of a face as one f32x2 pair)
     auto face_z = [&](int f, int lx, int j) -> T {  // between local planes j-1 and j of column lx
         const T *P = fz + f * NZP + lx;
         const T *M = fz + (NF + f) * NZP + lx;
-        return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
-               weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
+        if constexpr (BULK)
+            return weno5_pm(make_float2(P[j * TX], M[(j + 5) * TX]), make_float2(P[(j + 1) * TX], M[(j + 4) * TX]),
+                            make_float2(P[(j + 2) * TX], M[(j + 3) * TX]), make_float2(P[(j + 3) * TX], M[(j + 2) * TX]),
+                            make_float2(P[(j + 4) * TX], M[(j + 1) * TX]), eps);
+        else
+            return weno5<T>(P[j * TX], P[(j + 1) * TX], P[(j + 2) * TX], P[(j + 3) * TX], P[(j + 4) * TX], eps) +
+                   weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
     };
     T fzb[NF];
 #pragma unroll

@@ -233,6 +233,32 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
     return *reinterpret_cast<const float2 *>(&r);
 }
 
+// weno5 of a face's WENO(+) window (lane x) and its mirrored WENO(-) window
+// (lane y) at once, returning their sum (the face flux): the same operations
+// as weno5<float> on each lane; beta_2's (3 D2 - D1) is formed negated (it
+// enters squared only).
+__device__ __forceinline__ float weno5_pm(float2 a, float2 b, float2 c, float2 d, float2 e, float eps_)
+{
+    const float2 D1 = sub2(b, a), D2 = sub2(c, b), D3 = sub2(d, c), D4 = sub2(e, d);
+    const float2 t0 = sub2(D4, D3), t1 = sub2(D3, D2), t2 = sub2(D2, D1);
+    const float2 s0 = fma2(bc2(-3.0f), D3, D4), s1 = add2(D2, D3), s2 = fma2(bc2(-3.0f), D2, D1);
+    const float2 k13 = bc2((float)(13.0 / 12.0)), q = bc2(0.25f), eps = bc2(eps_);
+    float2 g0 = fma2(mul2(k13, t0), t0, fma2(mul2(q, s0), s0, eps));
+    float2 g1 = fma2(mul2(k13, t1), t1, fma2(mul2(q, s1), s1, eps));
+    float2 g2 = fma2(mul2(k13, t2), t2, fma2(mul2(q, s2), s2, eps));
+    g0 = mul2(g0, g0);
+    g1 = mul2(g1, g1);
+    g2 = mul2(g2, g2);
+    const float2 w0 = mul2(bc2(0.3f), mul2(g1, g2)), w1 = mul2(bc2(0.6f), mul2(g0, g2)),
+                 w2 = mul2(bc2(0.1f), mul2(g0, g1));
+    const float2 sw = add2(add2(w0, w1), w2);
+    const float2 num =
+        fma2(w0, sub2(t1, t0), fma2(mul2(bc2(-2.0f), w2), sub2(t1, t2), mul2(fma2(bc2(2.0f), D3, D2), sw)));
+    const float2 den = mul2(bc2(6.0f), sw);
+    const float2 v = fma2(num, make_float2(fast_rcp(den.x), fast_rcp(den.y)), c);
+    return v.x + v.y;
+}
+
 // weno5_slide for two streams at once (two components of the same line and
 // sign, stored as float2 pairs): the same operations in the same order on each
 // lane.  beta_2's (3 D2 - D1) enters only squared, so its negation D1 - 3 D2 is
