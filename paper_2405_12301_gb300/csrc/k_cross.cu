@@ -353,8 +353,16 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) {
                     const T *P = fp7[f], *M = fm7[f];
-                    const T Flo = weno5<T>(P[0], P[1], P[2], P[3], P[4], eps) + weno5<T>(M[5], M[4], M[3], M[2], M[1], eps);
-                    const T Fhi = weno5<T>(P[1], P[2], P[3], P[4], P[5], eps) + weno5<T>(M[6], M[5], M[4], M[3], M[2], eps);
+                    T Flo, Fhi;
+                    if constexpr (F64) {
+                        Flo = weno5<T>(P[0], P[1], P[2], P[3], P[4], eps) + weno5<T>(M[5], M[4], M[3], M[2], M[1], eps);
+                        Fhi = weno5<T>(P[1], P[2], P[3], P[4], P[5], eps) + weno5<T>(M[6], M[5], M[4], M[3], M[2], eps);
+                    } else {  // WENO(+) and the mirrored WENO(-) of an interface as one f32x2 pair
+                        Flo = weno5_pm(make_float2(P[0], M[5]), make_float2(P[1], M[4]), make_float2(P[2], M[3]),
+                                       make_float2(P[3], M[2]), make_float2(P[4], M[1]), eps);
+                        Fhi = weno5_pm(make_float2(P[1], M[6]), make_float2(P[2], M[5]), make_float2(P[3], M[4]),
+                                       make_float2(P[4], M[3]), make_float2(P[5], M[2]), eps);
+                    }
                     // out[f][l][i][r]: role 0/1 fix r (= j) and vary l (= v); role 2 fixes l, varies r
                     const long long o = (long long)f * S.n_left * n * S.n_right + outbase_j + v * outstride_v +
                                         (long long)i * S.n_right;
