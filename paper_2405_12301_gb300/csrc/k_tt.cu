@@ -38,15 +38,21 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
-// Sum over the 8-lane group of a lane (lanes 8g .. 8g+7).  The update loops
-// below give each column of a reflector update to one 8-lane group (4 columns
-// per warp, a lane every 8th row), so a column's dot product costs 3 shuffle
-// adds instead of 5 and every FP64 instruction serves 4 columns.
-__device__ __forceinline__ double group8_sum(double v)
+// The update loops below give each column of a reflector update to a group of
+// LPC lanes (CPW = 32 / LPC columns per warp, a lane every LPC-th row).  On
+// this GPU every FP64 warp instruction holds the FP64 pipe however many lanes
+// it serves, so the group's shuffle adds (log2 LPC per lane), the redundant
+// w = tau (dot + x_j) on every lane of the group and the one-lane diagonal
+// update are pure overhead on top of the 2 FMAs per row: 4 lanes keep it near
+// 15% (8 lanes cost about 35%).  Sub-blocks are stored with a pitch of b + 4
+// (b a multiple of 32), so a half-warp's 4 columns x 4 rows hit 16 distinct
+// banks.
+constexpr int LPC = 4, CPW = 32 / LPC, LDPAD = 4;
+
+__device__ __forceinline__ double group_sum(double v)
 {
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
 }
 
@@ -64,24 +70,24 @@ __device__ __forceinline__ void householder(double x0, double sig, double &beta,
     }
 }
 
-size_t qr_factor_smem(int k, int b) { return sizeof(double) * ((size_t)k * (b + 1) + (size_t)k * (k + 1) + k); }
+size_t qr_factor_smem(int k, int b) { return sizeof(double) * ((size_t)k * (b + LDPAD) + (size_t)k * (k + 1) + k); }
 size_t qr_apply_smem(int k, int b, int p)
 {
-    return sizeof(double) * ((size_t)k * (b + 1) + (size_t)p * (b + 1) + (size_t)p * (k + 1) + k);
+    return sizeof(double) * ((size_t)k * (b + LDPAD) + (size_t)p * (b + LDPAD) + (size_t)p * (k + 1) + k);
 }
 size_t svd_smem(int pk, int q) { return sizeof(double) * ((size_t)pk * (q + 1) + (size_t)pk * (pk + 1) + 2 * pk); }
 
 __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
 {
-    const QRDesc d = descs[blockIdx.y];
+    const QRDesc &d = descs[blockIdx.y];
     const int chunk = blockIdx.x;
     if (chunk >= d.chunks || d.m <= 0) return;
     extern __shared__ double sm[];
-    const int k = d.k, b = d.b, ldb = b + 1, ldr = k + 1;
+    const int k = d.k, b = d.b, ldb = b + LDPAD, ldr = k + 1;
     double *B = sm;                       // sub-block, column-major [k][ldb]
     double *R = B + (size_t)k * ldb;      // running R, column-major [k][ldr]
     double *ts = R + (size_t)k * ldr;     // taus of the current sub-block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sub = lane & 7;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / LPC, sub = lane % LPC;
     const long long r0 = (long long)chunk * d.chunk_rows;
     const long long r1 = min(d.m, r0 + d.chunk_rows);
 
@@ -117,16 +123,16 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
                 const double tau = ts[j];
                 if (tau != 0.0) {
                     const double *v = B + j * ldb;
-                    for (int c0 = j + 1 + warp * 4; c0 < k; c0 += TT_NW * 4) {
+                    for (int c0 = j + 1 + warp * CPW; c0 < k; c0 += TT_NW * CPW) {
                         const int c = c0 + grp;
                         const bool ok = c < k;
                         double *col = B + (ok ? c : 0) * ldb;
                         double w = 0.0;
                         if (ok)
-                            for (int i = j + 1 + sub; i < bs; i += 8) w = fma(v[i], col[i], w);
-                        w = (group8_sum(w) + (ok ? col[j] : 0.0)) * tau;
+                            for (int i = j + 1 + sub; i < bs; i += LPC) w = fma(v[i], col[i], w);
+                        w = (group_sum(w) + (ok ? col[j] : 0.0)) * tau;
                         if (ok)
-                            for (int i = j + 1 + sub; i < bs; i += 8) col[i] = fma(-v[i], w, col[i]);
+                            for (int i = j + 1 + sub; i < bs; i += LPC) col[i] = fma(-v[i], w, col[i]);
                         __syncwarp();
                         if (ok && sub == 0) col[j] -= w;
                     }
@@ -158,16 +164,16 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
                 const double tau = ts[j];
                 if (tau != 0.0) {
                     const double *y = B + j * ldb;
-                    for (int c0 = j + 1 + warp * 4; c0 < k; c0 += TT_NW * 4) {
+                    for (int c0 = j + 1 + warp * CPW; c0 < k; c0 += TT_NW * CPW) {
                         const int c = c0 + grp;
                         const bool ok = c < k;
                         double *col = B + (ok ? c : 0) * ldb;
                         double w = 0.0;
                         if (ok)
-                            for (int i = sub; i < bs; i += 8) w = fma(y[i], col[i], w);
-                        w = (group8_sum(w) + (ok ? R[c * ldr + j] : 0.0)) * tau;
+                            for (int i = sub; i < bs; i += LPC) w = fma(y[i], col[i], w);
+                        w = (group_sum(w) + (ok ? R[c * ldr + j] : 0.0)) * tau;
                         if (ok)
-                            for (int i = sub; i < bs; i += 8) col[i] = fma(-y[i], w, col[i]);
+                            for (int i = sub; i < bs; i += LPC) col[i] = fma(-y[i], w, col[i]);
                         __syncwarp();
                         if (ok && sub == 0) R[c * ldr + j] -= w;
                     }
@@ -190,16 +196,16 @@ __global__ void __launch_bounds__(TT_NT) k_qr_factor(const QRDesc *descs)
 
 __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
 {
-    const QApplyDesc d = descs[blockIdx.y];
+    const QApplyDesc &d = descs[blockIdx.y];
     const int chunk = blockIdx.x;
     if (chunk >= d.chunks || d.m <= 0 || d.p <= 0) return;
     extern __shared__ double sm[];
-    const int k = d.k, b = d.b, p = d.p, ldb = b + 1, ldx = k + 1;
+    const int k = d.k, b = d.b, p = d.p, ldb = b + LDPAD, ldx = k + 1;
     double *Y = sm;                        // reflectors of a sub-block, column-major [k][ldb]
     double *Z = Y + (size_t)k * ldb;       // output block, column-major [p][ldb]
     double *X = Z + (size_t)p * ldb;       // running top rows, column-major [p][ldx]
     double *ts = X + (size_t)p * ldx;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 3, sub = lane & 7;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane / LPC, sub = lane % LPC;
     const long long r0 = (long long)chunk * d.chunk_rows;
     const long long r1 = min(d.m, r0 + d.chunk_rows);
     const int nsub = (int)((r1 - r0 + b - 1) / b);
@@ -228,7 +234,7 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
         for (int e = threadIdx.x; e < bs * p; e += TT_NT) Z[(e / bs) * ldb + e % bs] = 0.0;
         for (int j = threadIdx.x; j < k; j += TT_NT) ts[j] = d.tau[((long long)chunk * d.sub_per_chunk + s) * k + j];
         __syncthreads();
-        for (int q0 = warp * 4; q0 < p; q0 += TT_NW * 4) {
+        for (int q0 = warp * CPW; q0 < p; q0 += TT_NW * CPW) {
             const int q = q0 + grp;
             const bool ok = q < p;
             double *zq = Z + (ok ? q : 0) * ldb;
@@ -239,10 +245,10 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
                 const double *y = Y + j * ldb;
                 double w = 0.0;
                 if (ok)
-                    for (int i = sub; i < bs; i += 8) w = fma(y[i], zq[i], w);
-                w = (group8_sum(w) + (ok ? xq[j] : 0.0)) * tau;
+                    for (int i = sub; i < bs; i += LPC) w = fma(y[i], zq[i], w);
+                w = (group_sum(w) + (ok ? xq[j] : 0.0)) * tau;
                 if (ok)
-                    for (int i = sub; i < bs; i += 8) zq[i] = fma(-y[i], w, zq[i]);
+                    for (int i = sub; i < bs; i += LPC) zq[i] = fma(-y[i], w, zq[i]);
                 __syncwarp();
                 if (ok && sub == 0) xq[j] -= w;
                 __syncwarp();
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
     }
     for (int j = threadIdx.x; j < k; j += TT_NT) ts[j] = d.tau[(long long)chunk * d.sub_per_chunk * k + j];
     __syncthreads();
-    for (int q0 = warp * 4; q0 < p; q0 += TT_NW * 4) {
+    for (int q0 = warp * CPW; q0 < p; q0 += TT_NW * CPW) {
         const int q = q0 + grp;
         const bool ok = q < p;
         double *zq = Z + (ok ? q : 0) * ldb;
@@ -273,10 +279,10 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
             const double *v = Y + j * ldb;
             double w = 0.0;
             if (ok)
-                for (int i = j + 1 + sub; i < b1; i += 8) w = fma(v[i], zq[i], w);
-            w = (group8_sum(w) + (ok ? zq[j] : 0.0)) * tau;
+                for (int i = j + 1 + sub; i < b1; i += LPC) w = fma(v[i], zq[i], w);
+            w = (group_sum(w) + (ok ? zq[j] : 0.0)) * tau;
             if (ok)
-                for (int i = j + 1 + sub; i < b1; i += 8) zq[i] = fma(-v[i], w, zq[i]);
+                for (int i = j + 1 + sub; i < b1; i += LPC) zq[i] = fma(-v[i], w, zq[i]);
             __syncwarp();
             if (ok && sub == 0) zq[j] -= w;
             __syncwarp();
