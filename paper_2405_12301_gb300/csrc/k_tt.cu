@@ -48,6 +48,15 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // (b a multiple of 32), so a half-warp's 4 columns x 4 rows hit 16 distinct
 // banks.
 constexpr int LPC = 4, CPW = 32 / LPC, LDPAD = 4;
+constexpr int SV_PPW = 4;  // Jacobi pairs per warp (8 lanes each)
+
+__device__ __forceinline__ double group8_sum_d(double v)
+{
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+    v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+    return v;
+}
 
 __device__ __forceinline__ double group_sum(double v)
 {
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(TT_NT) k_qr_apply(const QApplyDesc *descs)
 // One-sided Jacobi on the pk columns of M = T^T (column t = row t of T, length q).
 __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
 {
-    const SvdDesc d = descs[blockIdx.x];
+    const SvdDesc &d = descs[blockIdx.x];
     const int pk = d.pk, q = d.q;
     if (pk <= 0) return;
     extern __shared__ double sm[];
@@ -320,9 +329,11 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
     const int n = pk + (pk & 1);  // round-robin over an even count; index pk (odd case) is a bye
     const int npairs = n / 2;
     const double tol = 8.0 * (double)max(pk, q) * DBL_EPSILON;  // cosine below which a pair counts as orthogonal
-    // per round: the pairs' dot products (a warp per pair), their rotations (a
-    // lane per pair: the square roots and divisions run once per pair, not on
-    // every lane of a warp), then the rotations themselves (a warp per pair)
+    // per round: the pairs' dot products (an 8-lane group per pair, 4 pairs per
+    // warp: the group sums cost 3 shuffle adds, a warp sum 5, and the columns
+    // are at most 96 long), their rotations (a lane per pair: the square roots
+    // and divisions run once per pair, not on every lane of a group), then the
+    // rotations themselves (an 8-lane group per pair)
     __shared__ double s_a[TT_KMAX / 2], s_b[TT_KMAX / 2], s_c[TT_KMAX / 2], s_cs[TT_KMAX / 2], s_sn[TT_KMAX / 2];
     __shared__ int s_uv[TT_KMAX / 2][2];
     for (int sweep = 0; sweep < 60 && n > 1; ++sweep) {
@@ -330,21 +341,23 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
         __syncthreads();
         for (int round = 0; round < n - 1; ++round) {
             auto idx = [&](int t) { return t == 0 ? 0 : 1 + (t - 1 + round) % (n - 1); };
-            for (int slot = warp; slot < npairs; slot += TT_NW) {
-                const int u = idx(slot), v = idx(n - 1 - slot);
+            for (int s0 = warp * SV_PPW; s0 < npairs; s0 += TT_NW * SV_PPW) {  // the same trip count on every lane
+                const int slot = s0 + (lane >> 3), sub = lane & 7;
+                const bool ok = slot < npairs;
+                const int u = ok ? idx(slot) : 0, v = ok ? idx(n - 1 - slot) : 0;
                 double a = 0.0, bb = 0.0, c = 0.0;
-                if (u < pk && v < pk) {
+                if (ok && u < pk && v < pk) {
                     const double *mu = M + u * ldm, *mv = M + v * ldm;
-                    for (int i = lane; i < q; i += 32) {
+                    for (int i = sub; i < q; i += 8) {
                         a = fma(mu[i], mu[i], a);
                         bb = fma(mv[i], mv[i], bb);
                         c = fma(mu[i], mv[i], c);
                     }
-                    a = warp_sum_d(a);
-                    bb = warp_sum_d(bb);
-                    c = warp_sum_d(c);
                 }
-                if (lane == 0) {
+                a = group8_sum_d(a);
+                bb = group8_sum_d(bb);
+                c = group8_sum_d(c);
+                if (ok && sub == 0) {
                     s_a[slot] = a;
                     s_b[slot] = bb;
                     s_c[slot] = c;
@@ -367,19 +380,19 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
                 s_sn[slot] = sn;
             }
             __syncthreads();
-            for (int slot = warp; slot < npairs; slot += TT_NW) {
+            for (int slot = threadIdx.x >> 3; slot < npairs; slot += TT_NT / 8) {  // no shuffles: groups may leave early
                 const double sn = s_sn[slot];
                 if (sn == 0.0) continue;
                 const double cs = s_cs[slot];
-                const int u = s_uv[slot][0], v = s_uv[slot][1];
+                const int u = s_uv[slot][0], v = s_uv[slot][1], sub = lane & 7;
                 double *mu = M + u * ldm, *mv = M + v * ldm;
-                for (int i = lane; i < q; i += 32) {
+                for (int i = sub; i < q; i += 8) {
                     const double x = mu[i], y = mv[i];
                     mu[i] = cs * x - sn * y;
                     mv[i] = sn * x + cs * y;
                 }
                 double *vu = V + u * ldv, *vv = V + v * ldv;
-                for (int i = lane; i < pk; i += 32) {
+                for (int i = sub; i < pk; i += 8) {
                     const double x = vu[i], y = vv[i];
                     vu[i] = cs * x - sn * y;
                     vv[i] = sn * x + cs * y;
