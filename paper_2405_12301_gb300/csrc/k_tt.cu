@@ -48,13 +48,12 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // (b a multiple of 32), so a half-warp's 4 columns x 4 rows hit 16 distinct
 // banks.
 constexpr int LPC = 4, CPW = 32 / LPC, LDPAD = 4;
-constexpr int SV_PPW = 4;  // Jacobi pairs per warp (8 lanes each)
+constexpr int SV_LPP = 4, SV_PPW = 32 / SV_LPP;  // Jacobi lanes per pair, pairs per warp
 
-__device__ __forceinline__ double group8_sum_d(double v)
+__device__ __forceinline__ double pair_sum_d(double v)
 {
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 2);
-    v += __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+#pragma unroll
+    for (int o = SV_LPP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
 }
 
@@ -329,11 +328,11 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
     const int n = pk + (pk & 1);  // round-robin over an even count; index pk (odd case) is a bye
     const int npairs = n / 2;
     const double tol = 8.0 * (double)max(pk, q) * DBL_EPSILON;  // cosine below which a pair counts as orthogonal
-    // per round: the pairs' dot products (an 8-lane group per pair, 4 pairs per
-    // warp: the group sums cost 3 shuffle adds, a warp sum 5, and the columns
-    // are at most 96 long), their rotations (a lane per pair: the square roots
-    // and divisions run once per pair, not on every lane of a group), then the
-    // rotations themselves (an 8-lane group per pair)
+    // per round: the pairs' dot products (an SV_LPP-lane group per pair: its
+    // sums cost log2 SV_LPP shuffle adds, a warp sum 5, and the columns are at
+    // most 96 long), their rotations (a lane per pair: the square roots and
+    // divisions run once per pair, not on every lane of a group), then the
+    // rotations themselves (an SV_LPP-lane group per pair)
     __shared__ double s_a[TT_KMAX / 2], s_b[TT_KMAX / 2], s_c[TT_KMAX / 2], s_cs[TT_KMAX / 2], s_sn[TT_KMAX / 2];
     __shared__ int s_uv[TT_KMAX / 2][2];
     for (int sweep = 0; sweep < 60 && n > 1; ++sweep) {
@@ -342,21 +341,21 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
         for (int round = 0; round < n - 1; ++round) {
             auto idx = [&](int t) { return t == 0 ? 0 : 1 + (t - 1 + round) % (n - 1); };
             for (int s0 = warp * SV_PPW; s0 < npairs; s0 += TT_NW * SV_PPW) {  // the same trip count on every lane
-                const int slot = s0 + (lane >> 3), sub = lane & 7;
+                const int slot = s0 + lane / SV_LPP, sub = lane % SV_LPP;
                 const bool ok = slot < npairs;
                 const int u = ok ? idx(slot) : 0, v = ok ? idx(n - 1 - slot) : 0;
                 double a = 0.0, bb = 0.0, c = 0.0;
                 if (ok && u < pk && v < pk) {
                     const double *mu = M + u * ldm, *mv = M + v * ldm;
-                    for (int i = sub; i < q; i += 8) {
+                    for (int i = sub; i < q; i += SV_LPP) {
                         a = fma(mu[i], mu[i], a);
                         bb = fma(mv[i], mv[i], bb);
                         c = fma(mu[i], mv[i], c);
                     }
                 }
-                a = group8_sum_d(a);
-                bb = group8_sum_d(bb);
-                c = group8_sum_d(c);
+                a = pair_sum_d(a);
+                bb = pair_sum_d(bb);
+                c = pair_sum_d(c);
                 if (ok && sub == 0) {
                     s_a[slot] = a;
                     s_b[slot] = bb;
@@ -380,19 +379,19 @@ __global__ void __launch_bounds__(TT_NT) k_svd_jacobi(const SvdDesc *descs)
                 s_sn[slot] = sn;
             }
             __syncthreads();
-            for (int slot = threadIdx.x >> 3; slot < npairs; slot += TT_NT / 8) {  // no shuffles: groups may leave early
+            for (int slot = threadIdx.x / SV_LPP; slot < npairs; slot += TT_NT / SV_LPP) {  // no shuffles: groups may leave early
                 const double sn = s_sn[slot];
                 if (sn == 0.0) continue;
                 const double cs = s_cs[slot];
-                const int u = s_uv[slot][0], v = s_uv[slot][1], sub = lane & 7;
+                const int u = s_uv[slot][0], v = s_uv[slot][1], sub = lane % SV_LPP;
                 double *mu = M + u * ldm, *mv = M + v * ldm;
-                for (int i = sub; i < q; i += 8) {
+                for (int i = sub; i < q; i += SV_LPP) {
                     const double x = mu[i], y = mv[i];
                     mu[i] = cs * x - sn * y;
                     mv[i] = sn * x + cs * y;
                 }
                 double *vu = V + u * ldv, *vv = V + v * ldv;
-                for (int i = sub; i < pk; i += 8) {
+                for (int i = sub; i < pk; i += SV_LPP) {
                     const double x = vu[i], y = vv[i];
                     vu[i] = cs * x - sn * y;
                     vv[i] = sn * x + cs * y;
