@@ -155,6 +155,42 @@ def cpu_baseline(seconds=12.0):
             "host": host_info()}
 
 
+def _oracle_replica(seconds):
+    """One independent copy of the CPU baseline's sample, for the all-cores
+    run: (cell-stages done, seconds taken)."""
+    import oracle as O
+    from paper_2405_12301_gb300 import inputs as I
+    n = (256, 256)
+    cfg = O.Cfg(dim=2, n=n, lo=(0.0, 0.0), hi=(2.0, 2.0))
+    U = I.density_wave(2, n)
+    dt = O.cfl_dt(cfg, U, 0.5)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        U = O.ssprk3_step(cfg, U, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return n[0] * n[1] * 3 * steps, el
+
+
+def cpu_baseline_all_cores(seconds=6.0):
+    """The same oracle sample run as independent single-threaded copies, one
+    per core this process may use, at the same time (spawned processes; the
+    oracle itself is unchanged).  The value is the sum of the copies' rates."""
+    import multiprocessing as mp
+    try:
+        p = len(os.sched_getaffinity(0))
+    except AttributeError:
+        p = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(p) as pool:
+        res = pool.map(_oracle_replica, [seconds] * p)
+    value = sum(c / el for c, el in res) / 1e6
+    return {"value": value, "unit": "Mcell-stage/s", "cores": p, "kind": "oracle",
+            "sample": "%d concurrent copies of the 256^2 sample, ~%.0f s each, 1 thread each" % (p, seconds)}
+
+
 def host_info():
     """CPU model and the cores this process may run on (the oracle uses one)."""
     model = ""
@@ -709,6 +745,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
