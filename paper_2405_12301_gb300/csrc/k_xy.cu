@@ -91,6 +91,12 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
+    // b_n dt of the FP32-bulk stage combination, formed once per CTA (an FP64
+    // multiply holds the FP64 pipe for a whole warp however few lanes use it);
+    // read after the reference-state barrier
+    __shared__ float s_bdt;
+    if (BULK && EPI == EPI_STAGE && threadIdx.x == 0)
+        s_bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     // LF constants of the x and y splittings: the global alpha, or per direction
     const double alx = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha;
@@ -187,16 +193,8 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     const T alY = !PD ? alX : (BULK ? (T)f64_to_f32(aly) : (T)aly);
     const double gm1 = a.gamma - 1.0;
 
-    // split flux of a point in direction DIR, stored at its slot of fx / fy
-    auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
-        T fp[NF], fm[NF];
-        if constexpr (BULK) {
-            if (dirx) split_flux_diff<D, 0, true>(q, ref, alX, a.gm1_f, fp, fm);
-            else split_flux_diff<D, 1, true>(q, ref, alY, a.gm1_f, fp, fm);
-        } else {
-            if (dirx) split_flux_f64<D, 0, true>(q, alX, gm1, fp, fm);
-            else split_flux_f64<D, 1, true>(q, alY, gm1, fp, fm);
-        }
+    // split fluxes of a point in one direction, stored at its slot of fx / fy
+    auto split_store = [&](const T *fp, const T *fm, bool dirx, int lx, int ly) {
         if constexpr (L::PK) {
             float2 *b = dirx ? fx2 + ly * BXP2 + (lx + 3) : fy2 + (ly + 3) * TX + lx;
             const int np = dirx ? NXP2 : NYP;
@@ -220,6 +218,18 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
             }
         }
     };
+    // split flux of a point in direction DIR, stored at its slot of fx / fy
+    auto flux_store = [&](const T *q, bool dirx, int lx, int ly) {
+        T fp[NF], fm[NF];
+        if constexpr (BULK) {
+            if (dirx) split_flux_diff<D, 0, true>(q, ref, alX, a.gm1_f, fp, fm);
+            else split_flux_diff<D, 1, true>(q, ref, alY, a.gm1_f, fp, fm);
+        } else {
+            if (dirx) split_flux_f64<D, 0, true>(q, alX, gm1, fp, fm);
+            else split_flux_f64<D, 1, true>(q, alY, gm1, fp, fm);
+        }
+        split_store(fp, fm, dirx, lx, ly);
+    };
 
     {
         T q[NF];
@@ -233,8 +243,16 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = uk[f];
         }
-        flux_store(q, true, tx, ty);
-        flux_store(q, false, tx, ty);
+        if constexpr (L::PK) {  // both directions, sharing the direction-independent terms
+            float fp[2][NF], fm[2][NF];
+            const float al[2] = {alX, alY};
+            split_flux_diff_all<D>(q, ref, al, a.gm1_f, fp, fm);
+            split_store(fp[0], fm[0], true, tx, ty);
+            split_store(fp[1], fm[1], false, tx, ty);
+        } else {
+            flux_store(q, true, tx, ty);
+            flux_store(q, false, tx, ty);
+        }
     }
     if (halo) {
         T q[NF];
@@ -431,9 +449,7 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
         bool bad = false;
         if (own) {
             const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-            // the packed kernel re-reads dt rather than holding it through phase W
-            const double dte = L::PK ? a.ctl->dt : dt;
-            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dte);
+            const float bdt = s_bdt;
             float qn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {

@@ -417,6 +417,41 @@ __device__ __forceinline__ void split_flux_diff(const float *dq, const RefState<
     }
 }
 
+// split_flux_diff in every direction of one point, with the
+// direction-independent terms (rho, u, the kinetic and pressure differences)
+// formed once: per direction the same operations as split_flux_diff<D, DIR, true>.
+template <int D>
+__device__ __forceinline__ void split_flux_diff_all(const float *dq, const RefState<D> &r, const float *alpha, float gm1,
+                                                    float (*fp)[D + 2], float (*fm)[D + 2])
+{
+    constexpr int NF = D + 2;
+    const float rho = r.rho + dq[0];
+    const float ir = fast_rcp(rho);
+    float du[D], u[D];
+    float dk = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        du[e] = (dq[1 + e] - r.u[e] * dq[0]) * ir;
+        u[e] = r.u[e] + du[e];
+        dk += dq[1 + e] * u[e] + r.m[e] * du[e];
+    }
+    const float dp = gm1 * (dq[D + 1] - 0.5f * dk);
+    const float dH = dq[D + 1] + dp;
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+        float dF[NF];
+        dF[0] = dq[1 + dir];
+#pragma unroll
+        for (int e = 0; e < D; ++e) dF[1 + e] = dq[1 + e] * u[dir] + r.m[e] * du[dir] + (e == dir ? dp : 0.0f);
+        dF[D + 1] = du[dir] * (r.H + dH) + r.u[dir] * dH;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            fp[dir][f] = fmaf(alpha[dir], dq[f], dF[f]);
+            fm[dir][f] = fmaf(-alpha[dir], dq[f], dF[f]);
+        }
+    }
+}
+
 // ------------------------------------------------------------- wavespeed
 
 // |u| + sqrt(gamma p / rho) in FP64 with the operation order of the plain
