@@ -9,10 +9,11 @@
 //      reference state) and its LF split fluxes f(+/-) (Sec. 2.2) are formed in
 //      the directions that need them: each thread its own point in x and y, and
 //      one halo point in the halo's direction;
-//   W. every x- and y-interface flux of the tile is reconstructed once: each
-//      thread its cell's left and bottom faces for every component, and the
-//      tile's last column/row faces spread over the threads; WENO(+) plus
-//      mirrored WENO(-);
+//   W. every x- and y-interface flux of the tile is reconstructed once, WENO(+)
+//      plus mirrored WENO(-): in 2D as sliding runs along tile columns and row
+//      segments (FP32-bulk: component pairs in f32x2 arithmetic); in 3D planes
+//      each thread its cell's left and bottom faces for every component, and
+//      the tile's last column/row faces spread over the threads;
 //   C. each thread forms -(dF/dx) - (dG/dy) for its cell (Sec. 4.1) and either
 //      stores it (3D: the z sweep adds its part and runs the stage), writes L(U),
 //      or applies the SSP-RK3 stage combination (Eq. tt-ssprk3 without rounding)
