@@ -1,5 +1,5 @@
 // cross_internal.h -- descriptors of the pointwise residual at TT-cross
-// sample points (k_cross.cu), shared with the C ABI in weno_api.cu.
+// sample points (k_cross.cu), shared with the C ABI in api_cross.cu.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -33,7 +33,7 @@ constexpr int XT = 256;       // threads per CTA of k_cross_vecs
 constexpr int VP = 32;        // padded vector length (largest rank)
 constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 consecutive rows hit distinct banks
 // k_cross is compiled for several (threads per CTA, samples per chunk) pairs;
-// the autotuner of weno_api.cu picks one, and the persistent grid size, per
+// the autotuner of api_cross.cu picks one, and the persistent grid size, per
 // workload class.  Variant 0 is the default.
 // minb > 1 asks the compiler for registers that fit minb CTAs per SM.
 struct CrossVariant { int threads, chunk, minb; };

@@ -1,5 +1,5 @@
 // tt_internal.h -- declarations shared by the TT-algebra kernels (k_tt.cu,
-// k_maxvol.cu, k_cross_drv.cu) and the C ABI in weno_api.cu: descriptors of
+// k_maxvol.cu, k_cross_drv.cu) and the C ABI in api_tt.cu: descriptors of
 // the batched Householder QR, Q apply and Jacobi SVD of TT-rounding, of
 // maxvol, and of the TT-cross sweep's bookkeeping kernels.
 #pragma once
