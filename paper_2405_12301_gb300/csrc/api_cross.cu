@@ -123,8 +123,7 @@ static int cross_upload(weno_ctx *h, const CrossPrep &P, char *base, cudaStream_
 
 static void cross_config(const weno_ctx *h, const std::string &key, int &variant, int &cpsm)
 {
-    variant = 0;
-    cpsm = 4;
+    cross_default(&variant, &cpsm);
     auto it = h->tune.find(key);
     if (it != h->tune.end()) {
         variant = it->second.first;

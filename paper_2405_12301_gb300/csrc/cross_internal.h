@@ -46,6 +46,8 @@ cudaError_t launch_cross(const CrossArgs &a, int variant, int ctas_per_sm, cudaS
 int cross_max_rank();
 int cross_vec_len();
 int cross_num_variants();
+// The configuration used until the autotuner has timed a workload class.
+void cross_default(int *variant, int *ctas_per_sm);
 void cross_variant(int v, int *threads, int *chunk);
 cudaError_t cross_set_attributes();
 

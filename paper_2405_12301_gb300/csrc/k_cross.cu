@@ -34,12 +34,16 @@ constexpr int VP = 32;        // padded vector length (largest rank)
 constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 consecutive rows hit distinct banks
 // k_cross is compiled for several (threads per CTA, samples per chunk) pairs;
 // the autotuner of api_cross.cu picks one, and the persistent grid size, per
-// workload class.  Variant 0 is the default.
+// workload class.  Until then variant 5 at 3 CTAs per SM runs: held to 80
+// registers it keeps 24 warps per SM, where the unbounded builds (225
+// registers) fit one CTA per SM whatever grid is asked for.
 // minb > 1 asks the compiler for registers that fit minb CTAs per SM.
 struct CrossVariant { int threads, chunk, minb; };
 constexpr CrossVariant kCrossVariants[] = {{256, 64, 1}, {256, 32, 1}, {128, 64, 1}, {128, 32, 1},
                                            {256, 128, 1}, {256, 64, 3}, {128, 64, 6}};
 constexpr int kNumCrossVariants = sizeof(kCrossVariants) / sizeof(kCrossVariants[0]);
+static_assert(kCrossVariants[5].threads == 256 && kCrossVariants[5].chunk == 64 && kCrossVariants[5].minb == 3,
+              "cross_default names variant 5");
 
 template <typename T> __device__ __forceinline__ T cvtf(float x) { return (T)x; }
 
@@ -382,6 +386,11 @@ static size_t cross_dyn_bytes(bool f64, int chunk)
 
 int cross_vec_len() { return VP; }
 int cross_num_variants() { return kNumCrossVariants; }
+void cross_default(int *variant, int *ctas_per_sm)
+{
+    *variant = 5;  // {256, 64, 3}
+    *ctas_per_sm = 3;
+}
 void cross_variant(int v, int *threads, int *chunk)
 {
     *threads = kCrossVariants[v].threads;
