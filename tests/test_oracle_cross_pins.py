@@ -39,6 +39,22 @@ def test_maxvol_result_is_dominant_and_b_is_a_times_inverse():
     assert np.allclose(B, A @ np.linalg.inv(A[I]), atol=1e-10)
 
 
+def test_maxvol_is_unchanged_by_upper_triangular_mixing_of_columns():
+    """A and A R (R upper triangular, invertible) have the same maxvol rows,
+    swaps and B: column j of A R mixes only columns 0..j of A, so every
+    partial-pivoting residual of A R is a fixed multiple of A's, and
+    B = A A[I]^{-1} depends on the column space only.  (This is why the rows
+    maxvol picks from a fiber matrix and from its Householder Q agree.)"""
+    rng = np.random.default_rng(9)
+    for n, r in [(300, 12), (1000, 24), (40, 40)]:
+        A = rng.standard_normal((n, r))
+        R = np.triu(0.3 * rng.standard_normal((r, r)), 1) + np.diag(rng.uniform(0.5, 2.0, r) * rng.choice([-1, 1], r))
+        I1, B1, s1 = X.maxvol(A, delta=1e-2)
+        I2, B2, s2 = X.maxvol(A @ R, delta=1e-2)
+        assert I1.tolist() == I2.tolist() and s1 == s2
+        assert np.abs(B1 - B2).max() <= 1e-9 * max(1.0, np.abs(B1).max())
+
+
 def test_maxvol_finds_planted_rows():
     rng = np.random.default_rng(4)
     A = rng.standard_normal((100, 5)) * 0.01
