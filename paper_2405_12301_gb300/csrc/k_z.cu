@@ -65,18 +65,6 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
-    if (BULK) {
-        if (threadIdx.x < 32) {
-            const long long c0 = yoff + (long long)(z0 < nz ? z0 : nz - 1) * sz + (x0 < nx ? x0 : nx - 1);
-            double q[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
-            RefState<3> r;
-            make_ref<3>(q, a.gm1_f, r);
-            if (threadIdx.x == 0) ref = r;
-        }
-        __syncthreads();
-    }
     const T al = BULK ? (T)f64_to_f32(alpha) : (T)alpha;
     const double gm1 = a.gamma - 1.0;
     const bool interior = z0 >= 3 && z0 + TZ + 3 <= nz && x0 + TX <= nx;
@@ -112,9 +100,27 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         }
     };
 
+    // own and halo loads go out before the reference state's barrier, so their
+    // latency overlaps warp 0's work on the reference
     double uk[NF];
     float hk[NF], lk[NF];
     load_point(tx, tz, uk);
+    const bool halo = threadIdx.x < NHALO;
+    const int hx = threadIdx.x & 31, hz = (threadIdx.x >> 5) < 3 ? (threadIdx.x >> 5) - 3 : TZ + (threadIdx.x >> 5) - 3;
+    double qd[NF];
+    if (halo) load_point(hx, hz, qd);
+    if (BULK) {
+        if (threadIdx.x < 32) {
+            const long long c0 = yoff + (long long)(z0 < nz ? z0 : nz - 1) * sz + (x0 < nx ? x0 : nx - 1);
+            double q[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
+            RefState<3> r;
+            make_ref<3>(q, a.gm1_f, r);
+            if (threadIdx.x == 0) ref = r;
+        }
+        __syncthreads();
+    }
     {
         T q[NF];
         if constexpr (BULK) {
@@ -129,11 +135,8 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         }
         flux_store(q, tx, tz);
     }
-    if (threadIdx.x < NHALO) {
-        const int lx = threadIdx.x & 31, k = threadIdx.x >> 5;
-        const int lz = k < 3 ? k - 3 : TZ + k - 3;
-        double qd[NF];
-        load_point(lx, lz, qd);
+    if (halo) {
+        const int lx = hx, lz = hz;
         T q[NF];
         if constexpr (BULK) diff_from_ref<3>(qd, ref, q);
         else {
