@@ -434,3 +434,134 @@ def test_inflow_of_the_interior_state_keeps_a_free_stream():
     U = np.ascontiguousarray(np.broadcast_to(np.array(qs)[:, None, None, None], cfg.shape))
     R, _ = O.residual(cfg, U)
     assert np.abs(R).max() < 1e-12
+
+
+# ------------------------------------------- boundary, alpha and dt branches
+def _edge_pad(U, axis, k=3):
+    """U with k copies of its first and last cell along `axis` (numpy axis of the
+    [f][z][y][x] layout) prepended and appended, built by hand."""
+    lo = np.take(U, [0], axis=axis)
+    hi = np.take(U, [U.shape[axis] - 1], axis=axis)
+    return np.concatenate([lo] * k + [U] + [hi] * k, axis=axis)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_transmissive_ghosts_equal_a_padded_periodic_domain(dim):
+    """A transmissive side copies its edge cell into all three ghost layers (the
+    zero-order extrapolation read into Sec. 4.5's ghost fill).  The residual must
+    equal that of the state padded by hand with three copies of each edge cell,
+    on a periodic domain six cells wider per direction, restricted to the
+    original cells: their stencils reach at most three cells beyond the edge, so
+    the wrap-around of the padded domain never enters.  The state's edge cells
+    differ from their neighbours, so a clamp to the second cell or a mirror fill
+    changes the answer."""
+    n = (40,) if dim == 1 else (28, 22)
+    U = I.random_state(dim, n, seed=61, jumps=True)
+    for d in range(dim):
+        ax = 3 - d
+        edge = np.take(U, [0, 1, 2], axis=ax)
+        assert np.abs(np.diff(edge, axis=ax)).mean() > 1e-4
+    cfg = O.Cfg(dim=dim, n=n, bc=((O.TRANSMISSIVE, O.TRANSMISSIVE),) * 3)
+    a = O.alpha(cfg, U)
+    R = O.residual_dirs(cfg, U, a)
+    P = U
+    for d in range(dim):
+        P = _edge_pad(P, 3 - d)
+    h = [cfg.spacing(d) for d in range(dim)]
+    cp = O.Cfg(dim=dim, n=tuple(m + 6 for m in n), hi=tuple((m + 6) * hd for m, hd in zip(n, h)))
+    Rp = O.residual_dirs(cp, np.ascontiguousarray(P), a)
+    inner = Rp[..., 3:3 + n[0]] if dim == 1 else Rp[:, :, 3:3 + n[1], 3:3 + n[0]]
+    np.testing.assert_allclose(R, inner, rtol=0, atol=1e-13 * np.abs(R).max())
+    # the same state with a clamp to the second cell would not pass
+    Q = U.copy()
+    Q[..., 0] = Q[..., 1]
+    assert np.abs(O.residual_dirs(cfg, Q, a) - R).max() > 1e-6 * np.abs(R).max()
+
+
+def _speed_cells():
+    """(rho, u, v, w, p) of three cells whose direction-wise speeds |u_d| + a peak
+    in different cells, and a quiet cell (a = 1, at rest).  With gamma = 1.4:
+      A: rho 1.4,  p 1, a = 1, u = (2, 0.5, -0.25)  -> |u_d| + a = (3, 1.5, 1.25)
+      B: rho 0.35, p 1, a = 2, u = (0.5, -1.5, 0)   -> (2.5, 3.5, 2)
+      C: rho 1.4,  p 1, a = 1, u = (0, 0.1, -3)     -> (1, 1.1, 4)
+    so max_d = (3, 3.5, 4) by hand, and max(|u| + a) = 1 + sqrt(9.01) (cell C)."""
+    return [(1.4, 2.0, 0.5, -0.25, 1.0), (0.35, 0.5, -1.5, 0.0, 1.0), (1.4, 0.0, 0.1, -3.0, 1.0)], \
+        (1.4, 0.0, 0.0, 0.0, 1.0)
+
+
+def _state_with_cells(n, cells, quiet):
+    rho = np.full(n[::-1], quiet[0])
+    vel = [np.full(n[::-1], quiet[1 + d]) for d in range(3)]
+    p = np.full(n[::-1], quiet[4])
+    spots = [(0, 0, 1), (1, 2, 0), (2, 1, 3)]  # (z, y, x) of A, B, C
+    for (k, j, i), c in zip(spots, cells):
+        rho[k, j, i] = c[0]
+        for d in range(3):
+            vel[d][k, j, i] = c[1 + d]
+        p[k, j, i] = c[4]
+    return I.conserved(3, rho, vel, p)
+
+
+def test_per_direction_alpha_hand_values():
+    """Eq. (lax-friedrichs) read per direction: alpha_d = max over cells of
+    |u_d| + a.  Hand values (3, 3.5, 4) from three cells whose peaks sit in
+    different cells and need the absolute value (B's v and C's w are negative);
+    the global reading gives 1 + sqrt(9.01) in every direction."""
+    cells, quiet = _speed_cells()
+    n = (4, 3, 4)
+    U = _state_with_cells(n, cells, quiet)
+    cpd = O.Cfg(dim=3, n=n, alpha_mode=O.ALPHA_PER_DIR)
+    np.testing.assert_allclose(O.alpha(cpd, U), [3.0, 3.5, 4.0], rtol=1e-15)
+    cg = O.Cfg(dim=3, n=n)
+    np.testing.assert_allclose(O.alpha(cg, U), [1.0 + math.sqrt(9.01)] * 3, rtol=1e-15)
+    assert O.alpha_max(cpd, U) == pytest.approx(1.0 + math.sqrt(9.01), rel=1e-15)
+
+
+def test_per_direction_alpha_routes_alpha_y_to_the_y_splitting():
+    """A 2D state varying only in y with u = 0: in per-direction mode the y
+    splitting must take alpha_y = max(|v| + a), which is the 1D alpha of the
+    same profile along x, so the residual equals the 1D residual of (rho, rho v,
+    rho E) (rho E is the same since u = 0).  alpha_x = max(a) is smaller, so
+    handing it to the y direction would change the result."""
+    ny = 36
+    W = I.random_state(1, (ny,), seed=71, jumps=True)
+    rho = W[0]
+    v = W[1] / rho + 0.8
+    U1 = I.conserved(1, rho, [v], 0.4 * (W[2] - 0.5 * W[1] ** 2 / rho))
+    c1 = O.Cfg(dim=1, n=(ny,))
+    R1, a1 = O.residual(c1, U1)
+    nx = 4
+    c2 = O.Cfg(dim=2, n=(nx, ny), alpha_mode=O.ALPHA_PER_DIR)
+    U2 = np.zeros(c2.shape)
+    for f_src, f_dst in ((0, 0), (1, 2), (2, 3)):
+        U2[f_dst, 0] = U1[f_src, 0, 0][:, None]
+    a2 = O.alpha(c2, U2)
+    assert a2[1] == a1[0] and a2[0] < 0.8 * a2[1]
+    R2, _ = O.residual(c2, U2)
+    for i in range(nx):
+        np.testing.assert_allclose(R2[0, 0, :, i], R1[0, 0, 0], rtol=0, atol=1e-13 * np.abs(R1).max())
+        np.testing.assert_allclose(R2[2, 0, :, i], R1[1, 0, 0], rtol=0, atol=1e-13 * np.abs(R1).max())
+        np.testing.assert_allclose(R2[3, 0, :, i], R1[2, 0, 0], rtol=0, atol=1e-13 * np.abs(R1).max())
+        assert np.abs(R2[1, 0, :, i]).max() < 1e-13 * np.abs(R1).max()
+
+
+def test_cfl_dt_hand_value_on_an_anisotropic_grid():
+    """Eq. (cfl-other): dt = lambda h / max(|u| + a) with h the smallest spacing.
+    Grid spacings (0.25, 0.125, 0.5): h = 0.125 is the y spacing, so neither the
+    first nor the largest spacing passes; max(|u| + a) = 1 + sqrt(9.01) from
+    cell C (the per-direction maximum 4 would not pass either)."""
+    cells, quiet = _speed_cells()
+    n = (4, 4, 4)
+    U = _state_with_cells(n, cells, quiet)
+    cfg = O.Cfg(dim=3, n=n, hi=(1.0, 0.5, 2.0))
+    want = 0.4 * 0.125 / (1.0 + math.sqrt(9.01))
+    assert O.cfl_dt(cfg, U, 0.4) == pytest.approx(want, rel=1e-15)
+    # the run takes that dt for its first step
+    _, steps, t = O.run(cfg, U, 1.0, cfl=0.4, max_steps=1)
+    assert steps == 1 and t == pytest.approx(want, rel=1e-15)
+    # convergence-study rule: dt = min(CFL dt, c h^(5/3)), (1/8)^(5/3) = 1/32
+    _, steps, t = O.run(cfg, U, 1.0, cfl=0.4, dt_coef=0.01, max_steps=1)
+    assert steps == 1 and t == pytest.approx(0.01 / 32.0, rel=1e-14)
+    # the last step is shortened to land on t_end exactly
+    _, steps, t = O.run(cfg, U, 1.5 * want, cfl=0.4)
+    assert steps == 2 and t == 1.5 * want
