@@ -79,10 +79,18 @@ def load_peaks():
         return {}
 
 
-# FP32 FFMA pipe: 152 SMs x 128 lanes x 2 flop at the 2070 MHz maximum clock;
+# FP32 FFMA pipe: SMs x 128 lanes x 2 flop at the 2070 MHz maximum clock (the
+# SM count is queried from the device in main(); 152 on GB300);
 # FP64: the nominal 1.25 TFLOP/s of GB300.
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+SM_COUNT = 152
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2.070e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25
+
+
+def set_sm_count(n):
+    global SM_COUNT, PEAK_FP32_TFLOPS
+    SM_COUNT = int(n)
+    PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * 2.070e9 / 1e12
 
 
 class Clocks:
@@ -268,6 +276,30 @@ def accuracy(weno, I, torch, dim=2, N=256):
     return {"grid": list(n), "t": 2.0, "l1_rho_fp64": e64, "l1_rho_fp32_bulk": e32, "fp32_floor_l1": floor}
 
 
+def accuracy_headline(weno, I, torch, N=2048, t_end=0.05):
+    """L1 error of rho on the headline grid itself (2D density wave, 2048^2),
+    FP64 and FP32-bulk, against the exact advected wave at a short t_end (FP64
+    to t = 2 on this grid takes ~11k steps, minutes), and the FP32 floor."""
+    import numpy as np
+    n = (N, N)
+    U0 = I.density_wave(2, n)
+    ex = I.density_wave(2, n, t=t_end)[0]
+    out, steps = {}, {}
+    for prec in (weno.FP64, weno.FP32_BULK):
+        s = weno.Solver(2, n, (0.0, 0.0), (2.0, 2.0), precision=prec)
+        Ud = torch.from_numpy(U0).cuda()
+        s.set_time(0.0)
+        steps[prec] = s.run(Ud, t_end, graph_steps=32)
+        out[prec] = Ud[0].cpu().numpy()
+        s.close()
+        del Ud
+    e64 = float(np.abs(out[weno.FP64] - ex).mean())
+    e32 = float(np.abs(out[weno.FP32_BULK] - ex).mean())
+    floor = float(np.abs(out[weno.FP32_BULK] - out[weno.FP64]).mean())
+    return {"grid": list(n), "t": t_end, "steps": steps[weno.FP64], "steps_fp32_bulk": steps[weno.FP32_BULK],
+            "l1_rho_fp64": e64, "l1_rho_fp32_bulk": e32, "fp32_floor_l1": floor}
+
+
 def time_precision(weno, I, torch, w, prec, steps, warmup, dist, world):
     """Timed region: `steps` SSP-RK3 steps, every kernel bracketed by CUDA events
     on the launch stream.  Returns ms, per-kind kernel totals and launches."""
@@ -329,7 +361,7 @@ def roofline(w, prec_bulk, kms, kn, cells):
             "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
             "kernel": names[k], "ms_per_launch": per_launch_ms,
             "pipe": "fp32" if prec_bulk else "fp64",
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if prec_bulk
+            "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x 2070 MHz" % SM_COUNT if prec_bulk
             else "nominal GB300 FP64 1.25 TFLOP/s"}
 
 
@@ -644,6 +676,7 @@ def main():
 
     import torch
     torch.cuda.set_device(local)
+    set_sm_count(torch.cuda.get_device_properties(local).multi_processor_count)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -713,7 +746,11 @@ def main():
     cross = bench_cross(weno, I, torch, insts) if insts is not None else None
     ttr = bench_tt(weno, torch, insts) if insts is not None else None
     ttx = bench_tt_cross(weno, I, torch, insts) if insts is not None else None
-    acc = accuracy(weno, I, torch) if rank == 0 else None
+    acc = None
+    if rank == 0:
+        acc = accuracy(weno, I, torch)
+        if w["name"] == WORKLOADS["2d"]["name"]:
+            acc = {"grid_256_t2": acc, "headline_grid": accuracy_headline(weno, I, torch)}
     scalar = bench_scalar(weno, I, torch) if (rank == 0 and not args.no_cross) else None
     rl = roofline(w, True, kms, kn, cells)
     rl64 = roofline(w, False, kms64, kn64, cells)

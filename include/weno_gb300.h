@@ -117,7 +117,9 @@ int weno_init(weno_handle *out, const weno_grid *grid, const weno_params *params
 /* Frees the handle and its scratch (synchronises its stream first). */
 int weno_destroy(weno_handle h);
 
-/* Rebinds the stream used by later calls; drops any captured CUDA graph. */
+/* Rebinds the stream used by later calls.  Synchronises the old stream, then
+ * drops every captured CUDA graph of the handle (the step graph of weno_run and
+ * the replay graphs of weno_cross_eval); later calls capture them again. */
 int weno_set_stream(weno_handle h, void *cuda_stream);
 
 /* alpha_dev[0] = max over interior cells of |u| + sqrt(gamma p / rho) of U
@@ -203,8 +205,10 @@ int weno_profile_read(weno_handle h, double *ms, int64_t *launches, int64_t *tot
  *   sums_dev  device FP64 [nf], caller-owned, written asynchronously
  *   stream    cudaStream_t to enqueue on (NULL: legacy default stream)
  * The first call on each device looks up the device address of the scratch
- * array (with that device current); make that first call before any stream
- * capture.  All calls share the one scratch array and it keeps the last
+ * array (with that device current) and keeps it for the life of the process;
+ * make that first call before any stream capture.  The kept address does not
+ * survive cudaDeviceReset or a teardown of the device's primary context: do
+ * not call this entry point after either.  All calls share the one scratch array and it keeps the last
  * call's contents, so calls that overlap on the GPU (different streams, no
  * ordering between them) race and must not be issued.  Errors are returned as
  * a status; weno_last_error(NULL) then gives the reason. */

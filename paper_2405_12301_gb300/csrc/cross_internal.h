@@ -41,7 +41,7 @@ struct CrossArgs {
 };
 
 // variant: one of the compiled (threads per CTA, samples per chunk) pairs of
-// k_cross; ctas_per_sm: persistent grid of 152 x ctas_per_sm CTAs.
+// k_cross; ctas_per_sm: persistent grid of (SM count) x ctas_per_sm CTAs.
 cudaError_t launch_cross(const CrossArgs &a, int variant, int ctas_per_sm, cudaStream_t s);
 int cross_max_rank();
 int cross_vec_len();

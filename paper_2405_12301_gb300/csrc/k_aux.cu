@@ -177,11 +177,24 @@ cudaError_t launch_sums(const double *U, int nf, long long N, double *partials, 
     return cudaGetLastError();
 }
 
+int sm_count()
+{
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 cudaError_t launch_alpha(int model, int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl,
                          int slot, int per_dir, cudaStream_t s)
 {
     int blocks = (int)((N + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     if (blocks < 1) blocks = 1;
     if (model == MODEL_ADVECT) k_alpha_scalar<MODEL_ADVECT><<<blocks, 256, 0, s>>>(U, N, ctl, slot);
     if (model == MODEL_BURGERS) k_alpha_scalar<MODEL_BURGERS><<<blocks, 256, 0, s>>>(U, N, ctl, slot);

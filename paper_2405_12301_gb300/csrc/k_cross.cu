@@ -429,7 +429,7 @@ static cudaError_t launch_main(const CrossArgs &a, long long blocks, cudaStream_
     return cudaGetLastError();
 }
 
-// variant: index into kCrossVariants; ctas_per_sm: persistent grid = 152 x that
+// variant: index into kCrossVariants; ctas_per_sm: persistent grid = SM count x that
 // (capped by the number of work items).
 cudaError_t launch_cross(const CrossArgs &a, int variant, int ctas_per_sm, cudaStream_t s)
 {
@@ -440,7 +440,7 @@ cudaError_t launch_cross(const CrossArgs &a, int variant, int ctas_per_sm, cudaS
     else k_cross_vecs<false><<<a.n_sets, XT, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    long long blocks = 152LL * ctas_per_sm;
+    long long blocks = (long long)sm_count() * ctas_per_sm;
     if (blocks > a.n_work) blocks = a.n_work;
     if (blocks < 1) blocks = 1;
 #define X(V)                                                                             \

@@ -563,7 +563,7 @@ cudaError_t launch_tt_build(const TTSumDesc *d, int n, cudaStream_t s)
 
 cudaError_t launch_tt_contract(const TTSumDesc *d, int n, cudaStream_t s)
 {
-    k_tt_contract<<<dim3(152, n), 256, 0, s>>>(d);
+    k_tt_contract<<<dim3((unsigned)sm_count(), n), 256, 0, s>>>(d);
     return cudaGetLastError();
 }
 

@@ -194,6 +194,20 @@ extern "C" int weno_destroy(weno_handle h)
 extern "C" int weno_set_stream(weno_handle h, void *cuda_stream)
 {
     if (!h) return WENO_ERR_ARG;
+    // work already queued on the old stream (a graph replay included) finishes
+    // before its graphs go away
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->g_U = nullptr;
+        h->g_steps = 0;
+    }
+    for (auto &g : h->xgraphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaFree(g.buf);
+    }
+    h->xgraphs.clear();
     h->stream = (cudaStream_t)cuda_stream;
     return WENO_OK;
 }

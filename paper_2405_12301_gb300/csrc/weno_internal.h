@@ -53,5 +53,8 @@ cudaError_t launch_copy_alpha(const Ctl *ctl, int slot, double *out, cudaStream_
 cudaError_t launch_sums(const double *U, int nf, long long N, double *partials, int nblocks, double *out,
                         cudaStream_t s);
 int sums_blocks(long long N);
+// Number of SMs of the current device (queried once per device; persistent and
+// grid-stride launches are sized from it).
+int sm_count();
 
 }  // namespace wg

@@ -172,6 +172,13 @@ def weno_destroy(h):
     return _check(h, lib().weno_destroy(h))
 
 
+def weno_set_stream(h, stream=None):
+    """Binds a torch CUDA stream (default: the current one) to the handle."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return _check(h, lib().weno_set_stream(h, C.c_void_p(st.cuda_stream)))
+
+
 def weno_alpha(h, U, alpha_out):
     import torch
     return _check(h, lib().weno_alpha(h, _ptr(U, torch.float64), _ptr(alpha_out, torch.float64)))
@@ -462,6 +469,9 @@ class Solver:
 
     def sync(self):
         return weno_sync(self.h)
+
+    def set_stream(self, stream=None):
+        return weno_set_stream(self.h, stream)
 
     def profile_enable(self, enable=True):
         return weno_profile_enable(self.h, enable)

@@ -85,7 +85,7 @@ def test_2d_wave_fp64_and_fp32_bulk_orders(W):
     L1 errors, orders, and the FP32-bulk gate (within 1.1x of FP64 wherever FP64 is
     at least 10x the FP32 floor)."""
     rows = []
-    for N in (64, 128, 256):
+    for N in (64, 128, 256, 512):
         cfg = O.Cfg(dim=2, n=(N, N), lo=(0.0, 0.0), hi=(2.0, 2.0))
         U0 = I.density_wave(2, (N, N))
         ex = I.density_wave(2, (N, N), t=2.0)[0]
@@ -103,6 +103,40 @@ def test_2d_wave_fp64_and_fp32_bulk_orders(W):
     print("2D N=%d: L1 fp64 %.3e fp32-bulk %.3e floor %.3e" % rows[-1])
     orders = [math.log2(rows[k][1] / rows[k + 1][1]) for k in range(len(rows) - 1)]
     assert orders[-1] >= 4.8
+
+
+def test_2d_wave_1024_cfl05_fp64_and_fp32_bulk(W):
+    """Config 2 at 1024^2 with the CFL-0.5 step to t = 2 (the h^(5/3) rule would take
+    ~66k steps here): FP64 and FP32-bulk take the same number of steps, and the
+    FP32-bulk L1 error is within 1.1x of FP64 plus the floor (the L1 distance of
+    the two runs), both printed."""
+    N = 1024
+    cfg = O.Cfg(dim=2, n=(N, N), lo=(0.0, 0.0), hi=(2.0, 2.0))
+    U0 = I.density_wave(2, (N, N))
+    ex = I.density_wave(2, (N, N), t=2.0)[0]
+    u64, s64 = gpu_run(W, cfg, U0, 2.0, W.FP64)
+    u32, s32 = gpu_run(W, cfg, U0, 2.0, W.FP32_BULK)
+    e64 = np.abs(u64[0] - ex).mean()
+    e32 = np.abs(u32[0] - ex).mean()
+    floor = np.abs(u32[0] - u64[0]).mean()
+    print("2D N=1024 CFL 0.5: %d steps; L1 fp64 %.3e fp32-bulk %.3e floor %.3e" % (s64, e64, e32, floor))
+    assert s32 == s64
+    assert e32 <= 1.1 * e64 + floor
+
+
+def test_fp32_bulk_and_fp64_runs_take_the_same_steps(W):
+    """Both precisions take dt = lambda h / alpha from their own state's alpha
+    (FP32-bulk forms the wavespeeds in FP32, the max and dt in FP64); the two
+    alphas differ at the FP32 rounding level, so the step sequences to t = 2
+    have the same length and both land on t_end."""
+    for N in (64, 256):
+        cfg = O.Cfg(dim=2, n=(N, N), lo=(0.0, 0.0), hi=(2.0, 2.0))
+        U0 = I.density_wave(2, (N, N))
+        _, s64 = gpu_run(W, cfg, U0, 2.0, W.FP64)
+        _, s32 = gpu_run(W, cfg, U0, 2.0, W.FP32_BULK)
+        _, sref, _ = O.run(cfg, U0, 2.0, cfl=0.5) if N == 64 else (None, s64, None)
+        print("N=%d: steps fp64 %d, fp32-bulk %d, oracle %d" % (N, s64, s32, sref))
+        assert s32 == s64 == sref
 
 
 def test_2d_quadrant_256_run_matches_oracle(W):

@@ -175,6 +175,28 @@ def test_graph_run_equals_plain_steps_bitwise(W):
     assert torch.equal(a, b) and torch.equal(a, c)
 
 
+def test_set_stream_drops_the_step_graph_and_runs_on_the_new_stream(W):
+    """weno_set_stream synchronises the old stream and drops the captured step
+    graph; a run continued on a new stream captures again and gives bitwise the
+    result of plain steps on the original stream."""
+    cfg = O.Cfg(dim=2, n=(50, 40))
+    U0 = I.random_state(2, (50, 40), seed=14, jumps=True)
+    a, b = dev(U0), dev(U0)
+    s = solver(W, cfg)
+    s.set_time(0.0)
+    assert s.run(a, 1e9, max_steps=8, graph_steps=4) == 8
+    st = torch.cuda.Stream()
+    s.set_stream(st)
+    with torch.cuda.stream(st):
+        assert s.run(a, 1e9, max_steps=8, graph_steps=4) == 8
+    st.synchronize()
+    s.set_stream(torch.cuda.current_stream())
+    s2 = solver(W, cfg)
+    s2.set_time(0.0)
+    assert s2.run(b, 1e9, max_steps=16, graph_steps=0) == 16
+    assert torch.equal(a, b)
+
+
 def test_run_host_equals_device_run(W):
     cfg = O.Cfg(dim=2, n=(40, 36))
     U0 = I.random_state(2, (40, 36), seed=13)
