@@ -653,6 +653,16 @@ def bench_scalar(weno, I, torch, steps=4, warmup=3, N=256):
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"}}
 
 
+def pipe_peaks():
+    """Builds and runs the pipe-throughput probe (probe/pipe_peaks.cu): FFMA,
+    packed FFMA2, DFMA, MUFU rcp and conversion rates per clock per SM."""
+    src = os.path.join(ROOT, "paper_2405_12301_gb300", "probe", "pipe_peaks.cu")
+    exe = os.path.join(ROOT, "paper_2405_12301_gb300", "_build", "pipe_peaks")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
+    return subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -662,7 +672,7 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
-    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar"],
+    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar", "peaks"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--reps", type=int, default=5, help="timed calls of the --only measurement")
     args = ap.parse_args()
@@ -687,6 +697,9 @@ def main():
     from paper_2405_12301_gb300 import weno
 
     if args.only:
+        if args.only == "peaks":
+            print(pipe_peaks())
+            return
         if args.only == "scalar":
             print(json.dumps(bench_scalar(weno, I, torch)))
             return
