@@ -1,5 +1,6 @@
-// k_xy.cu -- fused x+y residual kernel of the WENO5-JS scheme for 2D grids
-// and for each z-plane of 3D grids.
+// k_xy.cu -- fused x+y residual kernel of the WENO5-JS scheme for 2D grids in
+// FP64 and for each z-plane of 3D grids (FP64 and FP32-bulk).  The 2D
+// FP32-bulk kernel is k_xy2 (k_xy2.cu).
 //
 // A CTA (256 threads) owns a TX x TY = 32 x 8 tile of one plane, one cell per
 // thread, and the plus-shaped halo around it (three ghost layers per side in x
@@ -11,8 +12,8 @@
 //      one halo point in the halo's direction;
 //   W. every x- and y-interface flux of the tile is reconstructed once, WENO(+)
 //      plus mirrored WENO(-): in 2D as sliding runs along tile columns and row
-//      segments (FP32-bulk: component pairs in f32x2 arithmetic); in 3D planes
-//      each thread its cell's left and bottom faces for every component, and
+//      segments; in 3D planes each thread its cell's left and bottom faces for
+//      every component (FP32-bulk: a face's two windows as one f32x2 pair), and
 //      the tile's last column/row faces spread over the threads;
 //   C. each thread forms -(dF/dx) - (dG/dy) for its cell (Sec. 4.1) and either
 //      stores it (3D: the z sweep adds its part and runs the stage), writes L(U),
@@ -35,9 +36,6 @@ constexpr int BXP = BX + 3;                 // row pitch of the x-flux points (4
                                             // runs of phase W read 8 rows x 4 components per
                                             // warp without bank conflicts)
 constexpr int NXP = BXP * TY;               // x-flux points: 38 (pitch 41) x 8
-constexpr int BXP2 = BX + 1;                // the same in float2 pairs (39: any odd pitch lets a
-                                            // warp's 8 rows x 4 segments of 64-bit reads hit
-                                            // distinct banks)
 constexpr int NYP = TX * BY;                // y-flux points: 32 x 14
 constexpr int NXI = (TX + 1) * TY;          // x interfaces: 33 x 8
 constexpr int NYI = TX * (TY + 1);          // y interfaces: 32 x 9
@@ -49,30 +47,26 @@ constexpr int NHALO = NHY + 6 * TY;         // plus x-halo points: 240
 // components) one thread per cell.
 template <int D> constexpr bool slide() { return D == 2; }
 
-// PK: the 2D FP32-bulk kernel keeps the four components as two float2 pairs,
-// (rho, m_x) and (m_y, E), in its flux and face arrays and reconstructs a pair
-// per sliding run with f32x2 arithmetic (half the issue slots of scalar FP32).
 template <int D, bool BULK> struct Layout {
     using T = typename std::conditional<BULK, float, double>::type;
     static constexpr int NF = D + 2;
-    static constexpr bool PK = D == 2 && BULK;
     static constexpr int NS = slide<D>() ? 2 : 1;                             // face-flux copies
-    static constexpr int NXPC = PK ? BXP2 * TY : NXP;                         // x-flux points per component
     static constexpr size_t F_off = 0;                                        // Fx, Fy
     static constexpr size_t fx_off = (sizeof(T) * NS * NF * (NXI + NYI) + 15) & ~size_t(15);
-    static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXPC;
+    static constexpr size_t fy_off = fx_off + sizeof(T) * 2 * NF * NXP;
     static constexpr size_t ref_off = (fy_off + sizeof(T) * 2 * NF * NYP + 15) & ~size_t(15);
     static constexpr size_t bytes = ref_off + sizeof(RefState<D>);
 };
 }  // namespace xy
 
-// The FP32-bulk kernels are held to 48 registers so that 5 CTAs (40 warps)
-// share an SM; their shared memory (about 42 KB) allows that many.
+// The FP32-bulk (3D plane) kernel is held to 48 registers so that 5 CTAs (40
+// warps) share an SM; its shared memory allows that many.
 template <int D, bool BULK, int EPI, bool PD>
 __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 {
     using namespace xy;
     using L = Layout<D, BULK>;
+    static_assert(!BULK || (D == 3 && EPI == EPI_STORE), "2D FP32-bulk runs in k_xy2");
     using T = typename L::T;
     constexpr int NF = L::NF;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -81,23 +75,12 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     T *fx = reinterpret_cast<T *>(smem + L::fx_off);       // [2][NF][TY][BXP]
     T *fy = reinterpret_cast<T *>(smem + L::fy_off);       // [2][NF][BY][TX]
     RefState<D> &ref = *reinterpret_cast<RefState<D> *>(smem + L::ref_off);
-    // PK views: [sign][pair] blocks of float2 (Fx2 [2][2][TY][TX+1], Fy2 [2][2][TY+1][TX],
-    // fx2 [2][2][TY][BXP2], fy2 [2][2][BY][TX])
-    float2 *Fx2 = reinterpret_cast<float2 *>(Fx), *Fy2 = reinterpret_cast<float2 *>(Fy);
-    float2 *fx2 = reinterpret_cast<float2 *>(fx), *fy2 = reinterpret_cast<float2 *>(fy);
-    constexpr int NXP2 = BXP2 * TY;
 
     // dt and alpha come from the control block; the FP32 path converts them on
     // the integer pipe (a cvt issues at FP64 rate on this GPU)
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
-    // b_n dt of the FP32-bulk stage combination, formed once per CTA (an FP64
-    // multiply holds the FP64 pipe for a whole warp however few lanes use it);
-    // read after the reference-state barrier
-    __shared__ float s_bdt;
-    if (BULK && EPI == EPI_STAGE && threadIdx.x == 0)
-        s_bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     // LF constants of the x and y splittings: the global alpha, or per direction
     const double alx = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha;
@@ -113,16 +96,10 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     const long long cell = zoff + (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
 
     // the stage combination needs U^n at this thread's cell: issue the loads now
-    // (the packed kernel loads it after phase W instead, and re-reads U^k and
-    // re-splits it there: holding them through the reconstruction would spill)
     double un[NF];
-    if (EPI == EPI_STAGE && a.stage > 0 && !L::PK) {
+    if (EPI == EPI_STAGE && a.stage > 0) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
-    }
-    if (EPI == EPI_STAGE && a.stage > 0 && L::PK) {  // bring U^n into L2 for the late read
-#pragma unroll
-        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Un + f * N + cell));
     }
 
     // interior tiles (halo inside the grid) skip the boundary rule
@@ -155,7 +132,6 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     // their loads go out before the reference state's barrier, so their latency
     // overlaps warp 0's work on the reference
     double uk[NF];                // U^(k) at the own cell, kept for the stage combination
-    float hk[NF], lk[NF];         // its hi/lo split (FP32-bulk)
     load_point(tx, ty, uk);
     const bool halo = threadIdx.x < NHALO;
     int hx = 0, hy = 0;
@@ -196,14 +172,7 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 
     // split fluxes of a point in one direction, stored at its slot of fx / fy
     auto split_store = [&](const T *fp, const T *fm, bool dirx, int lx, int ly) {
-        if constexpr (L::PK) {
-            float2 *b = dirx ? fx2 + ly * BXP2 + (lx + 3) : fy2 + (ly + 3) * TX + lx;
-            const int np = dirx ? NXP2 : NYP;
-            b[0] = make_float2(fp[0], fp[1]);
-            b[np] = make_float2(fp[2], fp[3]);
-            b[2 * np] = make_float2(fm[0], fm[1]);
-            b[3 * np] = make_float2(fm[2], fm[3]);
-        } else if (dirx) {
+        if (dirx) {
             const int o = ly * BXP + (lx + 3);
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -234,26 +203,13 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 
     {
         T q[NF];
-        if constexpr (BULK) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                split_f64(uk[f], hk[f], lk[f]);
-                q[f] = (hk[f] - ref.hi[f]) + (lk[f] - ref.lo[f]);
-            }
-        } else {
+        if constexpr (BULK) diff_from_ref<D>(uk, ref, q);
+        else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = uk[f];
         }
-        if constexpr (L::PK) {  // both directions, sharing the direction-independent terms
-            float fp[2][NF], fm[2][NF];
-            const float al[2] = {alX, alY};
-            split_flux_diff_all<D>(q, ref, al, a.gm1_f, fp, fm);
-            split_store(fp[0], fm[0], true, tx, ty);
-            split_store(fp[1], fm[1], false, tx, ty);
-        } else {
-            flux_store(q, true, tx, ty);
-            flux_store(q, false, tx, ty);
-        }
+        flux_store(q, true, tx, ty);
+        flux_store(q, false, tx, ty);
     }
     if (halo) {
         T q[NF];
@@ -294,36 +250,7 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
                    weno5<T>(M[(j + 5) * TX], M[(j + 4) * TX], M[(j + 3) * TX], M[(j + 2) * TX], M[(j + 1) * TX], eps);
     };
     T fxl[NF], fyb[NF];
-    if constexpr (L::PK) {
-        // One packed run of TY + 1 = 9 windows per thread (pair w & 1, sign (w >> 1) & 1):
-        //   warps 0-3, y: column `lane`, faces 0..8;
-        //   warps 4-7, x: row lane & 7, faces 8 s .. 8 s + 8 for s = lane >> 3 --
-        //      neighbouring segments share one face and write it with the same value.
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
-        const int blk = sg * 2 + pr;
-        const float2 *p;
-        float2 *out;
-        int st, os;
-        if (w < 4) {
-            p = fy2 + blk * NYP + lane;
-            out = Fy2 + blk * NYI + lane;
-            st = TX;
-            os = TX;
-        } else {
-            const int ly = lane & 7, j0 = (lane >> 3) * 8;
-            p = fx2 + blk * NXP2 + ly * BXP2 + j0;
-            out = Fx2 + blk * NXI + ly * (TX + 1) + j0;
-            st = 1;
-            os = 1;
-        }
-        if (sg) {  // WENO(-): the same run read backwards from the far end
-            p += (TY + 5) * st;
-            out += TY * os;
-            st = -st;
-            os = -os;
-        }
-        weno5_slide2<TY + 1>(p, st, (float)eps, out, os);
-    } else if constexpr (slide<D>()) {
+    if constexpr (slide<D>()) {
         // Two runs of TY + 1 = 9 windows per thread, one code path (a single
         // unrolled copy keeps the kernel inside the instruction cache):
         //   y: column `lane`, component w & 3, sign w >> 2, faces 0..8;
@@ -379,38 +306,13 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     }
     __syncthreads();
 
-    if constexpr (L::PK && EPI == EPI_STAGE) {  // U^n and U^k at the own cell (see above)
-        if (a.stage > 0) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
-        }
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            uk[f] = __ldg(a.U + f * N + cell);
-            split_f64(uk[f], hk[f], lk[f]);  // integer pipe; cheaper than holding them through phase W
-        }
-    }
-
     // ---- phase C: the cell's residual -(dF/dx) - (dG/dy) and the epilogue
     // face fluxes are twice F^: the halving rides on 1/h
     const T ihx = T(0.5) * (BULK ? (T)a.inv_h_f[0] : (T)a.inv_h[0]);
     const T ihy = T(0.5) * (BULK ? (T)a.inv_h_f[1] : (T)a.inv_h[1]);
     T r[NF];
-    if constexpr (L::PK) {
-        const float2 nihx = bc2(-(float)ihx), nihy = bc2(-(float)ihy);
 #pragma unroll
-        for (int pr = 0; pr < 2; ++pr) {  // F^ = WENO(+) + WENO(-), both signs' blocks
-            const int ox = pr * NXI + ty * (TX + 1) + tx, oy = pr * NYI + ty * TX + tx;
-            const float2 *FxM = Fx2 + 2 * NXI, *FyM = Fy2 + 2 * NYI;
-            const float2 dx = sub2(add2(Fx2[ox + 1], FxM[ox + 1]), add2(Fx2[ox], FxM[ox]));
-            const float2 dy = sub2(add2(Fy2[oy + TX], FyM[oy + TX]), add2(Fy2[oy], FyM[oy]));
-            const float2 rr = fma2(dy, nihy, mul2(dx, nihx));
-            r[2 * pr] = rr.x;
-            r[2 * pr + 1] = rr.y;
-        }
-    }
-#pragma unroll
-    for (int f = 0; f < (L::PK ? 0 : NF); ++f) {
+    for (int f = 0; f < NF; ++f) {
         T dx, dy;
         if constexpr (slide<D>()) {  // F^ = WENO(+) + WENO(-) at the right/top and left/bottom faces
             const int ox = f * NXI + ty * (TX + 1) + tx, oy = f * NYI + ty * TX + tx;
@@ -441,37 +343,8 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
         }
         return;
     }
-    // EPI_STAGE: U' = a_n U^n + b_n (U^k + dt R)
-    if constexpr (BULK) {
-        // U' = U^k + D, D = a_n (U^n - U^k) + b_n dt R in FP32 from hi/lo differences
-        float s = 0.0f, sd[D];
-#pragma unroll
-        for (int e = 0; e < D; ++e) sd[e] = 0.0f;
-        bool bad = false;
-        if (own) {
-            const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-            const float bdt = s_bdt;
-            float qn[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                float dl = bdt * r[f];
-                if (a.stage > 0) {
-                    float hn, ln;
-                    split_f64(un[f], hn, ln);
-                    dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
-                }
-                a.Uout[f * N + cell] = uk[f] + (double)dl;  // F2F on the FP64 pipe (it has room here)
-                qn[f] = hk[f] + (lk[f] + dl);
-            }
-            s = wavespeed_f32<D>(qn, a.gamma_f, bad);
-            if (PD && !bad) dirspeeds_f32<D>(qn, a.gamma_f, sd);
-        }
-        block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-        if constexpr (PD) {
-#pragma unroll
-            for (int e = 0; e < D; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
-        }
-    } else {
+    // EPI_STAGE (FP64): U' = a_n U^n + b_n (U^k + dt R)
+    if constexpr (!BULK) {
         double cmax = 0.0, sd[D];
 #pragma unroll
         for (int e = 0; e < D; ++e) sd[e] = 0.0;
@@ -520,8 +393,7 @@ cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStrea
     if (dim == D && bulk == B && epi == E)                    \
         return a.per_dir ? launch_xy_t<D, B, E, true>(a, s)   \
                          : launch_xy_t<D, B, E, false>(a, s);
-    X(2, false, EPI_RHS) X(2, false, EPI_STAGE) X(3, false, EPI_STORE)
-    X(2, true, EPI_RHS) X(2, true, EPI_STAGE) X(3, true, EPI_STORE)
+    X(2, false, EPI_RHS) X(2, false, EPI_STAGE) X(3, false, EPI_STORE) X(3, true, EPI_STORE)
 #undef X
     return cudaErrorInvalidValue;
 }

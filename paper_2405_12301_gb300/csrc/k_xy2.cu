@@ -1,0 +1,417 @@
+// k_xy2.cu -- the 2D FP32-bulk residual and SSP-RK3 stage kernel, in
+// pair-difference form.
+//
+// WENO5-JS (Sec. 2.2) depends on a stencil only through the first differences
+// of its values and its centre value, and the flux difference of a cell
+// (Eq. 1d-scalar-h-pde-fd) only through differences of interface fluxes.  With
+// F^_{j} = f(+)_{j-1} + c(+)_j + f(-)_j + c(-)_j (c the WENO correction to the
+// upwind centre value), the x part of a cell's residual is
+//   F^_{i+1} - F^_{i} = [f(+)_i - f(+)_{i-1}] + [f(-)_{i+1} - f(-)_i]
+//                       + [c(+)_{i+1} - c(+)_i] + [c(-)_{i+1} - c(-)_i],
+// so everything is built from the split-flux differences of neighbouring
+// points, D(a, b) = f(U_b) - f(U_a) (doubled: F +/- alpha U, see
+// split_flux_f64).  Each D is formed in FP32 from the two points' FP64 states
+// alone: dU = U_b - U_a from their hi/lo splits, then the exact
+// product-difference identities with a's FP32 primitives (d(xy) = dx y_b +
+// x_a dy, du = (dm - u_a drho) / rho_b), so it carries the FP32 relative
+// precision of the difference itself.  Consequences:
+//   * a face on a tile edge is formed by both CTAs that touch it from bitwise
+//     the same differences by the same operations, so it is the same number in
+//     both (no per-tile reference), and the periodic sums move only by the FP32
+//     rounding of the per-cell terms, which scales with neighbour differences;
+//   * the rounding of every WENO input scales with the difference of two
+//     neighbours, not with the variation across a tile.
+//
+// Stage state (Eq. tt-ssprk3 without rounding, written on increments): with
+// U^(k) = U^n + Delta_k, Delta_1 = dt L(U^n), Delta_2 = (Delta_1 + dt L(U^1)) / 4,
+// Delta_3 = 2 (Delta_2 + dt L(U^2)) / 3 and U^{n+1} = U^n + Delta_3.  Stage 1
+// splits U^n into FP32 hi/lo once and stores the split (hl) with Delta_1;
+// stages 2 and 3 read hl and Delta_{k-1} (FP32) instead of an FP64 state, so
+// no FP64 -> FP32 split is repeated, and only stage 3 touches FP64 arithmetic
+// (U^n + Delta_3, one DADD per field).
+//
+// A CTA of 256 threads owns a 32 x 8 tile, one cell per thread, plus the
+// plus-shaped halo of three ghost layers per side (Sec. 4.5).  Phases:
+//   A. every point of the tile and halo is loaded once (boundary rule on ghost
+//      indices) as FP32 hi/lo into shared memory;
+//   F. every neighbour pair is differenced once: each thread its own point's
+//      right (x) and upper (y) pair as one f32x2 computation (x pair in lane
+//      x, y pair in lane y), and one halo pair;
+//   W. WENO corrections of every face as sliding runs over the differences
+//      (weno5d_slide2), WENO(+) forward and the mirrored WENO(-) backward;
+//   C. the cell's residual from its two pairs and four face corrections per
+//      direction, then L(U) or the stage update and the block's wavespeed max.
+#include "weno_dev.cuh"
+#include "weno_internal.h"
+
+namespace wg {
+
+namespace xy2 {
+constexpr int NT = 256;
+constexpr int TX = 32, TY = 8;
+constexpr int NOWN = TX * TY;                 // 256 own points
+constexpr int XH0 = NOWN;                     // x-halo slots: [row][6] (cols -3..-1, TX..TX+2)
+constexpr int YH0 = XH0 + 6 * TY;             // y-halo slots: [6][col] (rows -3..-1, TY..TY+2)
+constexpr int NPT = YH0 + 6 * TX;             // 496 points
+constexpr int NHY = 6 * TX, NHALO = NHY + 6 * TY;  // 192 y-halo + 48 x-halo points
+constexpr int PX = TX + 5;                    // x pairs per row: a = col -3..TX+1
+constexpr int PXP = PX + 2;                   // their row pitch in float2 (odd: conflict-free runs)
+constexpr int PY = TY + 5;                    // y pairs per column: a = row -3..TY+1
+constexpr int NDX = PXP * TY;                 // one [sign][component pair] block of x differences
+constexpr int NDY = PY * TX;                  // one block of y differences
+constexpr int NFX = (TX + 1) * TY;            // x faces per block
+constexpr int NFY = TX * (TY + 1);            // y faces per block
+// shared memory: differences, then the points (phase A-F) or the faces (W-C)
+constexpr size_t DX_OFF = 0;
+constexpr size_t DY_OFF = DX_OFF + sizeof(float2) * 4 * NDX;
+constexpr size_t R_OFF = DY_OFF + sizeof(float2) * 4 * NDY;
+constexpr size_t PTS_BYTES = sizeof(float4) * 2 * NPT;
+constexpr size_t FACE_BYTES = sizeof(float2) * 4 * (NFX + NFY);
+constexpr size_t BYTES = R_OFF + (PTS_BYTES > FACE_BYTES ? PTS_BYTES : FACE_BYTES);
+
+__device__ __forceinline__ int own_slot(int lx, int ly) { return ly * TX + lx; }
+__device__ __forceinline__ int xh_slot(int lx, int ly) { return XH0 + ly * 6 + (lx < 0 ? lx + 3 : lx - TX + 3); }
+__device__ __forceinline__ int yh_slot(int lx, int ly) { return YH0 + (ly < 0 ? ly + 3 : ly - TY + 3) * TX + lx; }
+}  // namespace xy2
+
+// FP32 primitives of a point that only ever multiply differences.
+struct Prim2 {
+    float rho, u, v, H, mx, my;
+};
+
+__device__ __forceinline__ Prim2 prim2(const float4 h, float gm1)
+{
+    Prim2 P;
+    P.rho = h.x;
+    P.mx = h.y;
+    P.my = h.z;
+    const float ir = fast_rcp(h.x);
+    P.u = __fmul_rn(h.y, ir);
+    P.v = __fmul_rn(h.z, ir);
+    const float k = __fmaf_rn(h.z, P.v, __fmul_rn(h.y, P.u));
+    const float p = __fmul_rn(gm1, __fmaf_rn(-0.5f, k, h.w));
+    P.H = __fadd_rn(h.w, p);
+    return P;
+}
+
+// Doubled split-flux differences 2 (f(+/-)(U_b) - f(+/-)(U_a)) of two pairs at
+// once: lane x the x pair (a, bx), lane y the y pair (a, by).  Per lane the
+// normal momentum is n (x: m_x, y: m_y) and the other one t.  Outputs are
+// per component in the lane's own order (rho, n, t, E).
+__device__ __forceinline__ void pair_diff2(const float4 ha, const float4 la, const Prim2 &A, const float4 hbx,
+                                           const float4 lbx, const float4 hby, const float4 lby, float2 al,
+                                           float gm1, float2 *dp_out, float2 *dm_out)
+{
+    // dU = U_b - U_a from the hi/lo splits
+    const float2 dR = add2(sub2(make_float2(hbx.x, hby.x), bc2(ha.x)), sub2(make_float2(lbx.x, lby.x), bc2(la.x)));
+    const float2 dQ1 = add2(sub2(make_float2(hbx.y, hby.y), bc2(ha.y)), sub2(make_float2(lbx.y, lby.y), bc2(la.y)));
+    const float2 dQ2 = add2(sub2(make_float2(hbx.z, hby.z), bc2(ha.z)), sub2(make_float2(lbx.z, lby.z), bc2(la.z)));
+    const float2 dE = add2(sub2(make_float2(hbx.w, hby.w), bc2(ha.w)), sub2(make_float2(lbx.w, lby.w), bc2(la.w)));
+    const float2 dMn = make_float2(dQ1.x, dQ2.y), dMt = make_float2(dQ2.x, dQ1.y);
+    const float2 una = make_float2(A.u, A.v), uta = make_float2(A.v, A.u);
+    const float2 nuna = make_float2(-A.u, -A.v), nuta = make_float2(-A.v, -A.u);
+    const float2 mna = make_float2(A.mx, A.my), mta = make_float2(A.my, A.mx);
+    const float2 rb = add2(bc2(A.rho), dR);
+    const float2 irb = make_float2(fast_rcp(rb.x), fast_rcp(rb.y));
+    const float2 dun = mul2(fma2(nuna, dR, dMn), irb);  // du_n = (dm_n - u_n,a drho) / rho_b
+    const float2 dut = mul2(fma2(nuta, dR, dMt), irb);
+    const float2 unb = add2(una, dun), utb = add2(uta, dut);
+    const float2 kn = fma2(mna, dun, mul2(dMn, unb));  // d(m_n u_n)
+    const float2 dk = fma2(mta, dut, fma2(dMt, utb, kn));  // d(m . u)
+    const float2 dp = mul2(bc2(gm1), fma2(bc2(-0.5f), dk, dE));
+    const float2 dH = add2(dE, dp);
+    const float2 Fr = dMn;
+    const float2 Fn = add2(kn, dp);
+    const float2 Ft = fma2(mta, dun, mul2(dMt, unb));
+    const float2 FE = fma2(una, dH, mul2(dun, add2(bc2(A.H), dH)));
+    const float2 nal = make_float2(-al.x, -al.y);
+    dp_out[0] = fma2(al, dR, Fr);
+    dp_out[1] = fma2(al, dMn, Fn);
+    dp_out[2] = fma2(al, dMt, Ft);
+    dp_out[3] = fma2(al, dE, FE);
+    dm_out[0] = fma2(nal, dR, Fr);
+    dm_out[1] = fma2(nal, dMn, Fn);
+    dm_out[2] = fma2(nal, dMt, Ft);
+    dm_out[3] = fma2(nal, dE, FE);
+}
+
+template <int EPI, bool PD>
+__global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
+{
+    using namespace xy2;
+    constexpr int NF = 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *Dx = reinterpret_cast<float2 *>(smem + DX_OFF);   // [sign][pair][TY][PXP]
+    float2 *Dy = reinterpret_cast<float2 *>(smem + DY_OFF);   // [sign][pair][PY][TX]
+    float4 *Ph = reinterpret_cast<float4 *>(smem + R_OFF);    // [NPT] hi parts (phases A-F)
+    float4 *Pl = Ph + NPT;                                    // [NPT] lo parts
+    float2 *Fx = reinterpret_cast<float2 *>(smem + R_OFF);    // [sign][pair][TY][TX+1] (phases W-C)
+    float2 *Fy = Fx + 4 * NFX;                                // [sign][pair][TY+1][TX]
+
+    const long long dtbits = __double_as_longlong(a.ctl->dt);
+    if (a.check_dt && dtbits == 0) return;
+    const double dt = __longlong_as_double(dtbits);
+    __shared__ float s_bdt;
+    if (EPI == EPI_STAGE && threadIdx.x == 0)
+        s_bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
+    const float alY = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha);
+
+    const int nx = a.n[0], ny = a.n[1];
+    const long long N = a.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool own = gx < nx && gy < ny;
+    const long long cell = (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
+    // stage 1 reads U^n as FP64; stages 2 and 3 read the stored split and Delta_{k-1}
+    const bool from_hl = EPI == EPI_STAGE && a.stage > 0;
+    if (EPI == EPI_STAGE && a.stage == 2) {  // U^n at the own cell, for U^{n+1} = U^n + Delta_3
+#pragma unroll
+        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + cell));
+    }
+    const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
+
+    // ---- phase A: a point's FP32 hi/lo state, boundary rule on ghost indices
+    auto load_point = [&](int lx, int ly, float4 &h, float4 &l) {
+        int cx = x0 + lx, cy = y0 + ly;
+        bool fx_ = false, fy_ = false;
+        if (!interior) {
+            int inx, iny;
+            cx = cx < nx + 2 ? cx : nx + 2;
+            cy = cy < ny + 2 ? cy : ny + 2;
+            cx = ghost_map(cx, nx, a.bc[0][0], a.bc[0][1], fx_, inx);
+            cy = ghost_map(cy, ny, a.bc[1][0], a.bc[1][1], fy_, iny);
+            if (inx >= 0 || iny >= 0) {  // a ghost of an inflow side holds the given state
+                const double *st = inx >= 0 ? a.bc_state[0][inx] : a.bc_state[1][iny];
+                split_f64(st[0], h.x, l.x);
+                split_f64(st[1], h.y, l.y);
+                split_f64(st[2], h.z, l.z);
+                split_f64(st[3], h.w, l.w);
+                return;
+            }
+        }
+        const long long src = (long long)cy * nx + cx;
+        if (from_hl) {
+            const float2 *hl = a.hl + src;
+            const float *d = a.din + src;
+            const float2 q0 = __ldg(hl), q1 = __ldg(hl + N), q2 = __ldg(hl + 2 * N), q3 = __ldg(hl + 3 * N);
+            const float d0 = __ldg(d), d1 = __ldg(d + N), d2 = __ldg(d + 2 * N), d3 = __ldg(d + 3 * N);
+            h = make_float4(q0.x, q1.x, q2.x, q3.x);
+            l = make_float4(q0.y + d0, q1.y + d1, q2.y + d2, q3.y + d3);
+        } else {
+            const double *u = a.U + src;
+            split_f64(__ldg(u), h.x, l.x);
+            split_f64(__ldg(u + N), h.y, l.y);
+            split_f64(__ldg(u + 2 * N), h.z, l.z);
+            split_f64(__ldg(u + 3 * N), h.w, l.w);
+        }
+        if (fx_) { h.y = -h.y; l.y = -l.y; }
+        if (fy_) { h.z = -h.z; l.z = -l.z; }
+    };
+
+    const bool halo = threadIdx.x < NHALO;
+    int hk = 0, hslot = 0, bslot = 0;
+    bool hdirx = false, hpair = false;
+    {
+        float4 h, l;
+        load_point(tx, ty, h, l);
+        if (EPI == EPI_STAGE && a.stage == 0 && own) {  // the split of U^n, read by stages 2 and 3
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float hv = f == 0 ? h.x : f == 1 ? h.y : f == 2 ? h.z : h.w;
+                const float lv = f == 0 ? l.x : f == 1 ? l.y : f == 2 ? l.z : l.w;
+                a.hl[f * N + cell] = make_float2(hv, lv);
+            }
+        }
+        Ph[own_slot(tx, ty)] = h;
+        Pl[own_slot(tx, ty)] = l;
+    }
+    if (halo) {
+        int t = threadIdx.x, hx, hy;
+        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
+            hx = t & 31;
+            hk = t >> 5;
+            hy = hk < 3 ? hk - 3 : TY + hk - 3;
+            hslot = YH0 + hk * TX + hx;
+            // its upper pair, except from the last row; row -1's upper point is own row 0
+            bslot = hk == 2 ? own_slot(hx, 0) : YH0 + (hk + 1) * TX + hx;
+        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
+            t -= NHY;
+            hy = t / 6;
+            hk = t - hy * 6;
+            hx = hk < 3 ? hk - 3 : TX + hk - 3;
+            hdirx = true;
+            hslot = XH0 + hy * 6 + hk;
+            bslot = hk == 2 ? own_slot(0, hy) : XH0 + hy * 6 + hk + 1;
+        }
+        hpair = hk != 5;
+        float4 h, l;
+        load_point(hx, hy, h, l);
+        Ph[hslot] = h;
+        Pl[hslot] = l;
+    }
+    __syncthreads();
+
+    // ---- phase F: neighbour-pair differences
+    const float2 al = make_float2(alX, alY);
+    const float gm1 = a.gm1_f;
+    {
+        const int sa = own_slot(tx, ty);
+        const int sbx = tx + 1 < TX ? own_slot(tx + 1, ty) : xh_slot(TX, ty);
+        const int sby = ty + 1 < TY ? own_slot(tx, ty + 1) : yh_slot(tx, TY);
+        const float4 ha = Ph[sa], la = Pl[sa];
+        const Prim2 A = prim2(ha, gm1);
+        float2 dp[4], dm[4];
+        pair_diff2(ha, la, A, Ph[sbx], Pl[sbx], Ph[sby], Pl[sby], al, gm1, dp, dm);
+        // x pair (lane x: rho, m_x, m_y, E) at index tx + 3 of row ty
+        const int ix = ty * PXP + tx + 3;
+        Dx[0 * NDX + ix] = make_float2(dp[0].x, dp[1].x);
+        Dx[1 * NDX + ix] = make_float2(dp[2].x, dp[3].x);
+        Dx[2 * NDX + ix] = make_float2(dm[0].x, dm[1].x);
+        Dx[3 * NDX + ix] = make_float2(dm[2].x, dm[3].x);
+        // y pair (lane y: rho, m_y, m_x, E) at index ty + 3 of column tx
+        const int iy = (ty + 3) * TX + tx;
+        Dy[0 * NDY + iy] = make_float2(dp[0].y, dp[2].y);
+        Dy[1 * NDY + iy] = make_float2(dp[1].y, dp[3].y);
+        Dy[2 * NDY + iy] = make_float2(dm[0].y, dm[2].y);
+        Dy[3 * NDY + iy] = make_float2(dm[1].y, dm[3].y);
+    }
+    if (halo && hpair) {
+        const float4 ha = Ph[hslot], la = Pl[hslot], hb = Ph[bslot], lb = Pl[bslot];
+        const Prim2 A = prim2(ha, gm1);
+        float2 dp[4], dm[4];
+        pair_diff2(ha, la, A, hb, lb, hb, lb, al, gm1, dp, dm);  // the pair's own lane is used
+        if (hdirx) {
+            const int hy = (threadIdx.x - NHY) / 6;
+            const int ix = hy * PXP + (hk < 3 ? hk : TX + hk);  // a col + 3
+            Dx[0 * NDX + ix] = make_float2(dp[0].x, dp[1].x);
+            Dx[1 * NDX + ix] = make_float2(dp[2].x, dp[3].x);
+            Dx[2 * NDX + ix] = make_float2(dm[0].x, dm[1].x);
+            Dx[3 * NDX + ix] = make_float2(dm[2].x, dm[3].x);
+        } else {
+            const int hx = threadIdx.x & 31;
+            const int iy = (hk < 3 ? hk : TY + hk) * TX + hx;  // (a row + 3) * TX + col
+            Dy[0 * NDY + iy] = make_float2(dp[0].y, dp[2].y);
+            Dy[1 * NDY + iy] = make_float2(dp[1].y, dp[3].y);
+            Dy[2 * NDY + iy] = make_float2(dm[0].y, dm[2].y);
+            Dy[3 * NDY + iy] = make_float2(dm[1].y, dm[3].y);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase W: WENO corrections of every face (the points are dead now;
+    // the face arrays take their place).  One run of TY + 1 = 9 faces per
+    // thread, pair w & 1, sign (w >> 1) & 1:
+    //   warps 0-3, y: column `lane`, faces 0..8;
+    //   warps 4-7, x: row lane & 7, faces 8 s .. 8 s + 8 for s = lane >> 3
+    //   (neighbouring segments share one face and write the same value).
+    // Face j's WENO(+) window takes the pairs a = j-3..j (indices j..j+3), its
+    // mirrored WENO(-) window the pairs a = j+1..j-2 read backwards (indices
+    // j+4..j+1).  The differences hold 2 f(+/-): reconstruct with 4 eps.
+    {
+        const float eps = 4.0f * a.eps_f;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
+        const int blk = sg * 2 + pr;
+        const float2 *p;
+        float2 *out;
+        int st, os;
+        if (w < 4) {
+            p = Dy + blk * NDY + lane;
+            out = Fy + blk * NFY + lane;
+            st = TX;
+            os = TX;
+        } else {
+            const int ly = lane & 7, j0 = (lane >> 3) * 8;
+            p = Dx + blk * NDX + ly * PXP + j0;
+            out = Fx + blk * NFX + ly * (TX + 1) + j0;
+            st = 1;
+            os = 1;
+        }
+        if (sg) {  // WENO(-): differences j0+12 .. j0+1, faces j0+8 .. j0
+            p += 12 * st;
+            out += TY * os;
+            st = -st;
+            os = -os;
+        }
+        weno5d_slide2<TY + 1>(p, st, eps, sg ? -1.0f : 1.0f, out, os);
+    }
+    __syncthreads();
+
+    // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y from the cell's
+    // pairs (a = i-1 for f(+), a = i for f(-)) and its faces' corrections; the
+    // differences are doubled, so the halving rides on 1/h
+    float r[NF];
+    {
+        const float2 nihx = bc2(-0.5f * a.inv_h_f[0]), nihy = bc2(-0.5f * a.inv_h_f[1]);
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            const int dx = ty * PXP + tx + 2, fx = ty * (TX + 1) + tx;
+            const float2 sx = add2(add2(Dx[pr * NDX + dx], Dx[(2 + pr) * NDX + dx + 1]),
+                                   add2(sub2(Fx[pr * NFX + fx + 1], Fx[pr * NFX + fx]),
+                                        sub2(Fx[(2 + pr) * NFX + fx + 1], Fx[(2 + pr) * NFX + fx])));
+            const int dy = (ty + 2) * TX + tx, fy = ty * TX + tx;
+            const float2 sy = add2(add2(Dy[pr * NDY + dy], Dy[(2 + pr) * NDY + dy + TX]),
+                                   add2(sub2(Fy[pr * NFY + fy + TX], Fy[pr * NFY + fy]),
+                                        sub2(Fy[(2 + pr) * NFY + fy + TX], Fy[(2 + pr) * NFY + fy])));
+            const float2 rr = fma2(sy, nihy, mul2(sx, nihx));
+            r[2 * pr] = rr.x;
+            r[2 * pr + 1] = rr.y;
+        }
+    }
+    if (EPI == EPI_RHS) {
+        if (own) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a.Rout[f * N + cell] = f32_to_f64(r[f]);
+        }
+        return;
+    }
+    // EPI_STAGE: Delta_{k+1} = b_k (Delta_k + dt R); stage 3 ends the step
+    float s = 0.0f, sd[2] = {0.0f, 0.0f};
+    bool bad = false;
+    if (own) {
+        const float bdt = s_bdt;
+        const float cd = a.stage == 1 ? 0.25f : (float)(2.0 / 3.0);
+        float q[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            float d = bdt * r[f];
+            if (a.stage > 0) d = fmaf(cd, __ldg(a.din + f * N + cell), d);
+            if (a.stage < 2) a.dout[f * N + cell] = d;
+            else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
+            q[f] = a.hl[f * N + cell].x + d;  // the new state in FP32, for the wavespeed (stage 1 wrote hl)
+        }
+        s = wavespeed_f32<2>(q, a.gamma_f, bad);
+        if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);
+    }
+    block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+    if constexpr (PD) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
+    }
+}
+
+template <int EPI, bool PD>
+static cudaError_t launch_xy2_t(const SweepArgs &a, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_xy2<EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)xy2::BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)((a.n[0] + xy2::TX - 1) / xy2::TX), (unsigned)((a.n[1] + xy2::TY - 1) / xy2::TY), 1);
+    k_xy2<EPI, PD><<<grid, xy2::NT, xy2::BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xy2(int epi, const SweepArgs &a, cudaStream_t s)
+{
+    if (epi == EPI_RHS) return a.per_dir ? launch_xy2_t<EPI_RHS, true>(a, s) : launch_xy2_t<EPI_RHS, false>(a, s);
+    if (epi == EPI_STAGE) return a.per_dir ? launch_xy2_t<EPI_STAGE, true>(a, s) : launch_xy2_t<EPI_STAGE, false>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace wg

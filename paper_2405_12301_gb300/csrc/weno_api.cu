@@ -264,7 +264,8 @@ static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
     } else if (h->dim == 1) {
         CK(h, launch(h, 3, s, [&] { return launch_sweep(MODEL_EULER, 1, 0, bulk(h), last, a, s); }));
     } else if (h->dim == 2) {
-        CK(h, launch(h, 4, s, [&] { return launch_xy(2, bulk(h), last, a, s); }));
+        if (bulk(h)) CK(h, launch(h, 4, s, [&] { return launch_xy2(last, a, s); }));
+        else CK(h, launch(h, 4, s, [&] { return launch_xy(2, false, last, a, s); }));
     } else {
         CK(h, launch(h, 2, s, [&] { return launch_xy(3, bulk(h), EPI_STORE, a, s); }));
         CK(h, launch(h, 5, s, [&] { return launch_z(bulk(h), last, a, s); }));
@@ -279,11 +280,19 @@ static int enqueue_step(weno_ctx *h, double *U, cudaStream_t s)
     CK(h, launch(h, 7, s, [&] { return launch_step_begin(h->ctl, s); }));
     double *in[3] = {U, h->S1, h->S2};
     double *outs[3] = {h->S1, h->S2, U};
+    // 2D FP32-bulk keeps the split of U^n in S1 and the FP32 increments in S2
+    const bool inc = h->dim == 2 && bulk(h) && h->p.model == WENO_MODEL_EULER;
+    float *delta[2] = {reinterpret_cast<float *>(h->S2), reinterpret_cast<float *>(h->S2) + h->nf * h->N};
     for (int k = 0; k < 3; ++k) {
         SweepArgs a = base_args(h);
-        a.U = in[k];
+        a.U = inc ? U : in[k];
         a.Un = U;
-        a.Uout = outs[k];
+        a.Uout = inc ? (k == 2 ? U : nullptr) : outs[k];
+        if (inc) {
+            a.hl = reinterpret_cast<float2 *>(h->S1);
+            a.din = k > 0 ? delta[k - 1] : nullptr;
+            a.dout = k < 2 ? delta[k] : nullptr;
+        }
         a.stage = k;
         a.slot_in = k;
         a.slot_out = k + 1;

@@ -259,23 +259,25 @@ __device__ __forceinline__ float weno5_pm(float2 a, float2 b, float2 c, float2 d
     return v.x + v.y;
 }
 
-// weno5_slide for two streams at once (two components of the same line and
-// sign, stored as float2 pairs): the same operations in the same order on each
-// lane.  beta_2's (3 D2 - D1) enters only squared, so its negation D1 - 3 D2 is
-// formed instead (one FMA, and (q s) s is unchanged by the sign).
+// WENO5 of K consecutive windows along a line given the stencil's first
+// differences instead of its values (two streams as float2 pairs): window m
+// takes D1..D4 = p[m s], ..., p[(m + 3) s] and writes
+//   sign * (sum_r omega_r v^(r) - c)
+// to out[m os], c the window's centre value -- the same formula as weno5 with
+// the centre left out, so each window loads one new difference.  sign = -1
+// with a run read backwards gives the mirrored WENO(-) correction: a mirrored
+// window's differences are the negated forward ones, and the correction is odd
+// in the differences (beta and the weights are even, the numerator is linear).
 template <int K>
-__device__ __forceinline__ void weno5_slide2(const float2 *p, int s, float eps_, float2 *out, int os)
+__device__ __forceinline__ void weno5d_slide2(const float2 *p, int s, float eps_, float sign, float2 *out, int os)
 {
-    const float2 k13 = bc2((float)(13.0 / 12.0)), q = bc2(0.25f), eps = bc2(eps_);
-    const float2 v0 = *p, v1 = *(p += s);
-    float2 c = *(p += s), d = *(p += s);
-    float2 D1 = sub2(v1, v0), D2 = sub2(c, v1), D3 = sub2(d, c);
+    const float2 k13 = bc2((float)(13.0 / 12.0)), q = bc2(0.25f), eps = bc2(eps_), six = bc2(6.0f * sign);
+    float2 D1 = *p, D2 = *(p += s), D3 = *(p += s);
     float2 t1 = sub2(D3, D2), t2 = sub2(D2, D1);
     float2 A1 = fma2(mul2(k13, t1), t1, eps), A2 = fma2(mul2(k13, t2), t2, eps);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-        const float2 e = *(p += s);
-        const float2 D4 = sub2(e, d);
+        const float2 D4 = *(p += s);
         const float2 t0 = sub2(D4, D3);
         const float2 A0 = fma2(mul2(k13, t0), t0, eps);
         const float2 s0 = fma2(bc2(-3.0f), D3, D4), s1 = add2(D2, D3), s2 = fma2(bc2(-3.0f), D2, D1);
@@ -288,8 +290,8 @@ __device__ __forceinline__ void weno5_slide2(const float2 *p, int s, float eps_,
         const float2 sw = add2(add2(w0, w1), w2);
         const float2 num =
             fma2(w0, sub2(t1, t0), fma2(mul2(bc2(-2.0f), w2), sub2(t1, t2), mul2(fma2(bc2(2.0f), D3, D2), sw)));
-        const float2 den = mul2(bc2(6.0f), sw);
-        *out = fma2(num, make_float2(fast_rcp(den.x), fast_rcp(den.y)), c);
+        const float2 den = mul2(six, sw);
+        *out = mul2(num, make_float2(fast_rcp(den.x), fast_rcp(den.y)));
         out += os;
         D1 = D2;
         D2 = D3;
@@ -298,8 +300,6 @@ __device__ __forceinline__ void weno5_slide2(const float2 *p, int s, float eps_,
         t1 = t0;
         A2 = A1;
         A1 = A0;
-        c = d;
-        d = e;
     }
 }
 
@@ -413,41 +413,6 @@ __device__ __forceinline__ void split_flux_diff(const float *dq, const RefState<
         } else {
             fp[f] = 0.5f * (dF[f] + alpha * dq[f]);
             fm[f] = 0.5f * (dF[f] - alpha * dq[f]);
-        }
-    }
-}
-
-// split_flux_diff in every direction of one point, with the
-// direction-independent terms (rho, u, the kinetic and pressure differences)
-// formed once: per direction the same operations as split_flux_diff<D, DIR, true>.
-template <int D>
-__device__ __forceinline__ void split_flux_diff_all(const float *dq, const RefState<D> &r, const float *alpha, float gm1,
-                                                    float (*fp)[D + 2], float (*fm)[D + 2])
-{
-    constexpr int NF = D + 2;
-    const float rho = r.rho + dq[0];
-    const float ir = fast_rcp(rho);
-    float du[D], u[D];
-    float dk = 0.0f;
-#pragma unroll
-    for (int e = 0; e < D; ++e) {
-        du[e] = (dq[1 + e] - r.u[e] * dq[0]) * ir;
-        u[e] = r.u[e] + du[e];
-        dk += dq[1 + e] * u[e] + r.m[e] * du[e];
-    }
-    const float dp = gm1 * (dq[D + 1] - 0.5f * dk);
-    const float dH = dq[D + 1] + dp;
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) {
-        float dF[NF];
-        dF[0] = dq[1 + dir];
-#pragma unroll
-        for (int e = 0; e < D; ++e) dF[1 + e] = dq[1 + e] * u[dir] + r.m[e] * du[dir] + (e == dir ? dp : 0.0f);
-        dF[D + 1] = du[dir] * (r.H + dH) + r.u[dir] * dH;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            fp[dir][f] = fmaf(alpha[dir], dq[f], dF[f]);
-            fm[dir][f] = fmaf(-alpha[dir], dq[f], dF[f]);
         }
     }
 }

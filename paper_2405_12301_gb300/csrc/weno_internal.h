@@ -18,6 +18,11 @@ struct SweepArgs {
     double *Uout;        // U^(k+1)
     void *acc;           // residual accumulator: float (FP32-bulk) or double (FP64)
     double *Rout;        // output of EPI_RHS
+    // 2D FP32-bulk stage state (k_xy2): the FP32 hi/lo split of U^n, written
+    // by stage 1, and the FP32 increments Delta_k = U^(k) - U^n
+    float2 *hl;          // [nf][N]
+    const float *din;    // Delta_k read by stages 2 and 3
+    float *dout;         // Delta_{k+1} written by stages 1 and 2
     Ctl *ctl;
     long long N;         // cells per field (field stride)
     int n[3];
@@ -41,6 +46,8 @@ cudaError_t launch_sweep(int model, int dim, int dir, bool bulk, int epi, const 
 cudaError_t sweep_set_attributes();
 // Fused x+y residual of a 2D grid (EPI_RHS / EPI_STAGE) or of the z-planes of a 3D grid (EPI_STORE).
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
+// 2D FP32-bulk residual / stage in pair-difference form (EPI_RHS / EPI_STAGE).
+cudaError_t launch_xy2(int epi, const SweepArgs &a, cudaStream_t s);
 // z direction of a 3D grid, adding the accumulator and ending the residual (EPI_RHS / EPI_STAGE).
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
 

@@ -3,11 +3,12 @@
 // FP64 DFMA, the MUFU reciprocal and the FP64 -> FP32 conversion.
 //
 // Each kernel runs long dependency-free streams of one instruction kind (8
-// independent accumulators per thread, 16 resident warps per SM sub-partition
-// at most) on every SM, and every CTA reads the SM clock around its loop, so
-// the result is in operations per clock per SM, independent of the clock the
-// GPU ran at.  The host also times the whole launch with CUDA events, which
-// gives operations per second.  Output: one JSON line per pipe.
+// independent accumulators per thread) on every SM, launched as exactly one
+// wave (as many CTAs per SM as can be resident, at most 8), and every CTA reads
+// the SM clock around its loop, so the result is in operations per clock per
+// SM, independent of the clock the GPU ran at.  The host also times the whole
+// launch with CUDA events, which gives operations per second.  Output: one
+// JSON line per pipe.
 #include <cstdio>
 #include <cstdlib>
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ __global__ void __launch_bounds__(NT) k_pipe(int iters, float seed, float *sink)
     const float2 m2 = make_float2(m, m), c2 = make_float2(c, c);
     __syncthreads();
     const unsigned long long t0 = clock64();
+#pragma unroll 1
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(NT) k_pipe(int iters, float seed, float *sink)
                 if (KIND == 0) a[k] = fmaf(a[k], m, c);
                 if (KIND == 1) p[k] = __ffma2_rn(p[k], m2, c2);
                 if (KIND == 2) d[k] = fma(d[k], 0.9999, 1e-4);
-                if (KIND == 3) asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(a[k]));
+                if (KIND == 3) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k]));
                 if (KIND == 4) a[k] = __double2float_rn((double)a[k] * 0.9999);
             }
         }
@@ -58,9 +60,12 @@ __global__ void __launch_bounds__(NT) k_pipe(int iters, float seed, float *sink)
 template <int KIND>
 static void run(const char *name, int ops_per_inst, int blocks_per_sm, int iters)
 {
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, resident = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_pipe<KIND>, NT, 0);
+    if (resident < blocks_per_sm) blocks_per_sm = resident;
+    if (blocks_per_sm < 1) return;
     const int blocks = sms * blocks_per_sm;
     if (blocks > 4096) return;
     float *sink = nullptr;
