@@ -672,7 +672,7 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
-    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar", "peaks"],
+    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar", "peaks", "step"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--reps", type=int, default=5, help="timed calls of the --only measurement")
     args = ap.parse_args()
@@ -702,6 +702,13 @@ def main():
             return
         if args.only == "scalar":
             print(json.dumps(bench_scalar(weno, I, torch)))
+            return
+        if args.only == "step":  # the FP32-bulk timed region of --workload alone
+            w = WORKLOADS[args.workload]
+            ms, kms, kn, launches, _ = time_precision(weno, I, torch, w, weno.FP32_BULK, args.steps, args.warmup,
+                                                      None, 1)
+            print(json.dumps({"workload": w["name"], "ms_per_step": ms / args.steps,
+                              "kernels_ms_per_launch": kernel_table(kms, kn)}))
             return
         insts = tt_workload(I, torch)
         if args.only == "cross":

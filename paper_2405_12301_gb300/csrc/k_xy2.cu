@@ -74,23 +74,27 @@ __device__ __forceinline__ int xh_slot(int lx, int ly) { return XH0 + ly * 6 + (
 __device__ __forceinline__ int yh_slot(int lx, int ly) { return YH0 + (ly < 0 ? ly + 3 : ly - TY + 3) * TX + lx; }
 }  // namespace xy2
 
-// FP32 primitives of a point that only ever multiply differences.
+// FP32 primitives of a point (state hi + lo) that only ever multiply
+// differences.  They must describe the point's current state to FP32 relative
+// precision: in stages 2 and 3 the lo part carries Delta_k, which is far larger
+// than FP32 rounding, so hi alone (U^n) would not do.
 struct Prim2 {
     float rho, u, v, H, mx, my;
 };
 
-__device__ __forceinline__ Prim2 prim2(const float4 h, float gm1)
+__device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1)
 {
     Prim2 P;
-    P.rho = h.x;
-    P.mx = h.y;
-    P.my = h.z;
-    const float ir = fast_rcp(h.x);
-    P.u = __fmul_rn(h.y, ir);
-    P.v = __fmul_rn(h.z, ir);
-    const float k = __fmaf_rn(h.z, P.v, __fmul_rn(h.y, P.u));
-    const float p = __fmul_rn(gm1, __fmaf_rn(-0.5f, k, h.w));
-    P.H = __fadd_rn(h.w, p);
+    P.rho = __fadd_rn(h.x, l.x);
+    P.mx = __fadd_rn(h.y, l.y);
+    P.my = __fadd_rn(h.z, l.z);
+    const float E = __fadd_rn(h.w, l.w);
+    const float ir = fast_rcp(P.rho);
+    P.u = __fmul_rn(P.mx, ir);
+    P.v = __fmul_rn(P.my, ir);
+    const float k = __fmaf_rn(P.my, P.v, __fmul_rn(P.mx, P.u));
+    const float p = __fmul_rn(gm1, __fmaf_rn(-0.5f, k, E));
+    P.H = __fadd_rn(E, p);
     return P;
 }
 
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const int sbx = tx + 1 < TX ? own_slot(tx + 1, ty) : xh_slot(TX, ty);
         const int sby = ty + 1 < TY ? own_slot(tx, ty + 1) : yh_slot(tx, TY);
         const float4 ha = Ph[sa], la = Pl[sa];
-        const Prim2 A = prim2(ha, gm1);
+        const Prim2 A = prim2(ha, la, gm1);
         float2 dp[4], dm[4];
         pair_diff2(ha, la, A, Ph[sbx], Pl[sbx], Ph[sby], Pl[sby], al, gm1, dp, dm);
         // x pair (lane x: rho, m_x, m_y, E) at index tx + 3 of row ty
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
     if (halo && hpair) {
         const float4 ha = Ph[hslot], la = Pl[hslot], hb = Ph[bslot], lb = Pl[bslot];
-        const Prim2 A = prim2(ha, gm1);
+        const Prim2 A = prim2(ha, la, gm1);
         float2 dp[4], dm[4];
         pair_diff2(ha, la, A, hb, lb, hb, lb, al, gm1, dp, dm);  // the pair's own lane is used
         if (hdirx) {

@@ -1,6 +1,6 @@
 // pipe_peaks.cu -- throughput of the GB300 arithmetic pipes the roofline of
 // this library's kernels is stated against: FP32 FFMA, packed FFMA2 (f32x2),
-// FP64 DFMA, the MUFU reciprocal and the FP64 -> FP32 conversion.
+// FP64 DFMA and the FP64 <-> FP32 conversions.
 //
 // Each kernel runs long dependency-free streams of one instruction kind (8
 // independent accumulators per thread) on every SM, launched as exactly one
@@ -43,7 +43,6 @@ __global__ void __launch_bounds__(NT) k_pipe(int iters, float seed, float *sink)
                 if (KIND == 0) a[k] = fmaf(a[k], m, c);
                 if (KIND == 1) p[k] = __ffma2_rn(p[k], m2, c2);
                 if (KIND == 2) d[k] = fma(d[k], 0.9999, 1e-4);
-                if (KIND == 3) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k]));
                 if (KIND == 4) a[k] = __double2float_rn((double)a[k] * 0.9999);
             }
         }
@@ -105,7 +104,6 @@ int main()
     run<0>("ffma_f32", 2, 8, 4096);
     run<1>("ffma2_f32x2 (one instruction, two FMAs)", 4, 8, 4096);
     run<2>("dfma_f64", 2, 8, 512);
-    run<3>("mufu_rcp_approx_f32", 1, 8, 1024);
     run<4>("cvt f32->f64, DMUL, cvt f64->f32 (one op = the three)", 1, 8, 256);
     return 0;
 }
