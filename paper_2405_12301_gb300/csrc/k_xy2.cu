@@ -9,8 +9,8 @@
 //   F^_{i+1} - F^_{i} = [f(+)_i - f(+)_{i-1}] + [f(-)_{i+1} - f(-)_i]
 //                       + [c(+)_{i+1} - c(+)_i] + [c(-)_{i+1} - c(-)_i],
 // so everything is built from the split-flux differences of neighbouring
-// points, D(a, b) = f(U_b) - f(U_a) (doubled: F +/- alpha U, see
-// split_flux_f64).  Each D is formed in FP32 from the two points' FP64 states
+// points, D(a, b) = f(U_b) - f(U_a) (stored scaled for weno5d_slide2, see
+// pair_diff2).  Each D is formed in FP32 from the two points' FP64 states
 // alone: dU = U_b - U_a from their hi/lo splits, then the exact
 // product-difference identities with a's FP32 primitives (d(xy) = dx y_b +
 // x_a dy, du = (dm - u_a drho) / rho_b), so it carries the FP32 relative
@@ -98,12 +98,14 @@ __device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1
     return P;
 }
 
-// Doubled split-flux differences 2 (f(+/-)(U_b) - f(+/-)(U_a)) of two pairs at
-// once: lane x the x pair (a, bx), lane y the y pair (a, by).  Per lane the
-// normal momentum is n (x: m_x, y: m_y) and the other one t.  Outputs are
-// per component in the lane's own order (rho, n, t, E).
+// Split-flux differences of two pairs at once: lane x the x pair (a, bx),
+// lane y the y pair (a, by).  Per lane the normal momentum is n (x: m_x,
+// y: m_y) and the other one t.  Outputs, per component in the lane's own order
+// (rho, n, t, E), are scaled for weno5d_slide2: dp = (f(+)(U_b) - f(+)(U_a)) / 3
+// and dm = -(f(-)(U_b) - f(-)(U_a)) / 3 (the mirrored WENO(-) runs read the
+// negated differences), formed as (F +/- alpha U) differences times 1/6.
 __device__ __forceinline__ void pair_diff2(const float4 ha, const float4 la, const Prim2 &A, const float4 hbx,
-                                           const float4 lbx, const float4 hby, const float4 lby, float2 al,
+                                           const float4 lbx, const float4 hby, const float4 lby, float2 al6,
                                            float gm1, float2 *dp_out, float2 *dm_out)
 {
     // dU = U_b - U_a from the hi/lo splits
@@ -124,19 +126,20 @@ __device__ __forceinline__ void pair_diff2(const float4 ha, const float4 la, con
     const float2 dk = fma2(mta, dut, fma2(dMt, utb, kn));  // d(m . u)
     const float2 dp = mul2(bc2(gm1), fma2(bc2(-0.5f), dk, dE));
     const float2 dH = add2(dE, dp);
-    const float2 Fr = dMn;
-    const float2 Fn = add2(kn, dp);
-    const float2 Ft = fma2(mta, dun, mul2(dMt, unb));
-    const float2 FE = fma2(una, dH, mul2(dun, add2(bc2(A.H), dH)));
-    const float2 nal = make_float2(-al.x, -al.y);
-    dp_out[0] = fma2(al, dR, Fr);
-    dp_out[1] = fma2(al, dMn, Fn);
-    dp_out[2] = fma2(al, dMt, Ft);
-    dp_out[3] = fma2(al, dE, FE);
-    dm_out[0] = fma2(nal, dR, Fr);
-    dm_out[1] = fma2(nal, dMn, Fn);
-    dm_out[2] = fma2(nal, dMt, Ft);
-    dm_out[3] = fma2(nal, dE, FE);
+    const float2 sixth = bc2((float)(1.0 / 6.0));
+    const float2 Fr = mul2(sixth, dMn);
+    const float2 Fn = mul2(sixth, add2(kn, dp));
+    const float2 Ft = mul2(sixth, fma2(mta, dun, mul2(dMt, unb)));
+    const float2 FE = mul2(sixth, fma2(una, dH, mul2(dun, add2(bc2(A.H), dH))));
+    // (F + alpha dU) / 6 and -(F - alpha dU) / 6 = alpha dU / 6 - F / 6
+    dp_out[0] = fma2(al6, dR, Fr);
+    dp_out[1] = fma2(al6, dMn, Fn);
+    dp_out[2] = fma2(al6, dMt, Ft);
+    dp_out[3] = fma2(al6, dE, FE);
+    dm_out[0] = fma2(al6, dR, make_float2(-Fr.x, -Fr.y));
+    dm_out[1] = fma2(al6, dMn, make_float2(-Fn.x, -Fn.y));
+    dm_out[2] = fma2(al6, dMt, make_float2(-Ft.x, -Ft.y));
+    dm_out[3] = fma2(al6, dE, make_float2(-FE.x, -FE.y));
 }
 
 template <int EPI, bool PD>
@@ -215,25 +218,13 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         if (fy_) { h.z = -h.z; l.z = -l.z; }
     };
 
+    // the own point and the halo point of this thread: both loads go out
+    // before either is stored, so their latencies overlap
     const bool halo = threadIdx.x < NHALO;
-    int hk = 0, hslot = 0, bslot = 0;
-    bool hdirx = false, hpair = false;
-    {
-        float4 h, l;
-        load_point(tx, ty, h, l);
-        if (EPI == EPI_STAGE && a.stage == 0 && own) {  // the split of U^n, read by stages 2 and 3
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const float hv = f == 0 ? h.x : f == 1 ? h.y : f == 2 ? h.z : h.w;
-                const float lv = f == 0 ? l.x : f == 1 ? l.y : f == 2 ? l.z : l.w;
-                a.hl[f * N + cell] = make_float2(hv, lv);
-            }
-        }
-        Ph[own_slot(tx, ty)] = h;
-        Pl[own_slot(tx, ty)] = l;
-    }
+    int hk = 0, hslot = 0, bslot = 0, hx = 0, hy = 0;
+    bool hdirx = false;
     if (halo) {
-        int t = threadIdx.x, hx, hy;
+        int t = threadIdx.x;
         if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
             hx = t & 31;
             hk = t >> 5;
@@ -250,16 +241,29 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
             hslot = XH0 + hy * 6 + hk;
             bslot = hk == 2 ? own_slot(0, hy) : XH0 + hy * 6 + hk + 1;
         }
-        hpair = hk != 5;
-        float4 h, l;
-        load_point(hx, hy, h, l);
-        Ph[hslot] = h;
-        Pl[hslot] = l;
+    }
+    const bool hpair = halo && hk != 5;
+    {
+        float4 h, l, h2, l2;
+        load_point(tx, ty, h, l);
+        if (halo) load_point(hx, hy, h2, l2);
+        if (EPI == EPI_STAGE && a.stage == 0 && own) {  // the split of U^n, read by stages 2 and 3
+            a.hl[cell] = make_float2(h.x, l.x);
+            a.hl[N + cell] = make_float2(h.y, l.y);
+            a.hl[2 * N + cell] = make_float2(h.z, l.z);
+            a.hl[3 * N + cell] = make_float2(h.w, l.w);
+        }
+        Ph[own_slot(tx, ty)] = h;
+        Pl[own_slot(tx, ty)] = l;
+        if (halo) {
+            Ph[hslot] = h2;
+            Pl[hslot] = l2;
+        }
     }
     __syncthreads();
 
     // ---- phase F: neighbour-pair differences
-    const float2 al = make_float2(alX, alY);
+    const float2 al = make_float2(alX * (float)(1.0 / 6.0), alY * (float)(1.0 / 6.0));
     const float gm1 = a.gm1_f;
     {
         const int sa = own_slot(tx, ty);
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         Dy[2 * NDY + iy] = make_float2(dm[0].y, dm[2].y);
         Dy[3 * NDY + iy] = make_float2(dm[1].y, dm[3].y);
     }
-    if (halo && hpair) {
+    if (hpair) {
         const float4 ha = Ph[hslot], la = Pl[hslot], hb = Ph[bslot], lb = Pl[bslot];
         const Prim2 A = prim2(ha, la, gm1);
         float2 dp[4], dm[4];
@@ -305,6 +309,17 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
     __syncthreads();
 
+    // the epilogue's own-cell inputs, loaded now so that phase W hides their
+    // latency: Delta_k (stages 2, 3) and the hi part of U^n (its wavespeed)
+    float dk[NF] = {0.0f, 0.0f, 0.0f, 0.0f}, hn[NF] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (EPI == EPI_STAGE && own) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            hn[f] = a.hl[f * N + cell].x;  // stage 1 wrote it in phase A (a plain, coherent load)
+            if (a.stage > 0) dk[f] = __ldg(a.din + f * N + cell);
+        }
+    }
+
     // ---- phase W: WENO corrections of every face (the points are dead now;
     // the face arrays take their place).  One run of TY + 1 = 9 faces per
     // thread, pair w & 1, sign (w >> 1) & 1:
@@ -313,9 +328,9 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     //   (neighbouring segments share one face and write the same value).
     // Face j's WENO(+) window takes the pairs a = j-3..j (indices j..j+3), its
     // mirrored WENO(-) window the pairs a = j+1..j-2 read backwards (indices
-    // j+4..j+1).  The differences hold 2 f(+/-): reconstruct with 4 eps.
+    // j+4..j+1).  The runs return twice the corrections (see weno5d_slide2).
     {
-        const float eps = 4.0f * a.eps_f;
+        const float Geps = (float)(4.0 / 9.0) * a.eps_f;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
         const int blk = sg * 2 + pr;
         const float2 *p;
@@ -339,24 +354,26 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
             st = -st;
             os = -os;
         }
-        weno5d_slide2<TY + 1>(p, st, eps, sg ? -1.0f : 1.0f, out, os);
+        weno5d_slide2<TY + 1>(p, st, Geps, out, os);
     }
     __syncthreads();
 
     // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y from the cell's
-    // pairs (a = i-1 for f(+), a = i for f(-)) and its faces' corrections; the
-    // differences are doubled, so the halving rides on 1/h
+    // pairs (a = i-1 for f(+), a = i for f(-)) and its faces' corrections:
+    // twice the flux difference is 6 (Dt(+) - Dt(-)) + the doubled corrections'
+    // differences (Dt(-) holds the negated f(-) difference), and the halving
+    // rides on 1/h
     float r[NF];
     {
         const float2 nihx = bc2(-0.5f * a.inv_h_f[0]), nihy = bc2(-0.5f * a.inv_h_f[1]);
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
             const int dx = ty * PXP + tx + 2, fx = ty * (TX + 1) + tx;
-            const float2 sx = add2(add2(Dx[pr * NDX + dx], Dx[(2 + pr) * NDX + dx + 1]),
+            const float2 sx = fma2(bc2(6.0f), sub2(Dx[pr * NDX + dx], Dx[(2 + pr) * NDX + dx + 1]),
                                    add2(sub2(Fx[pr * NFX + fx + 1], Fx[pr * NFX + fx]),
                                         sub2(Fx[(2 + pr) * NFX + fx + 1], Fx[(2 + pr) * NFX + fx])));
             const int dy = (ty + 2) * TX + tx, fy = ty * TX + tx;
-            const float2 sy = add2(add2(Dy[pr * NDY + dy], Dy[(2 + pr) * NDY + dy + TX]),
+            const float2 sy = fma2(bc2(6.0f), sub2(Dy[pr * NDY + dy], Dy[(2 + pr) * NDY + dy + TX]),
                                    add2(sub2(Fy[pr * NFY + fy + TX], Fy[pr * NFY + fy]),
                                         sub2(Fy[(2 + pr) * NFY + fy + TX], Fy[(2 + pr) * NFY + fy])));
             const float2 rr = fma2(sy, nihy, mul2(sx, nihx));
@@ -381,10 +398,10 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             float d = bdt * r[f];
-            if (a.stage > 0) d = fmaf(cd, __ldg(a.din + f * N + cell), d);
+            if (a.stage > 0) d = fmaf(cd, dk[f], d);
             if (a.stage < 2) a.dout[f * N + cell] = d;
             else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
-            q[f] = a.hl[f * N + cell].x + d;  // the new state in FP32, for the wavespeed (stage 1 wrote hl)
+            q[f] = hn[f] + d;  // the new state in FP32, for the wavespeed
         }
         s = wavespeed_f32<2>(q, a.gamma_f, bad);
         if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);

@@ -259,40 +259,50 @@ __device__ __forceinline__ float weno5_pm(float2 a, float2 b, float2 c, float2 d
     return v.x + v.y;
 }
 
-// WENO5 of K consecutive windows along a line given the stencil's first
-// differences instead of its values (two streams as float2 pairs): window m
-// takes D1..D4 = p[m s], ..., p[(m + 3) s] and writes
-//   sign * (sum_r omega_r v^(r) - c)
-// to out[m os], c the window's centre value -- the same formula as weno5 with
-// the centre left out, so each window loads one new difference.  sign = -1
-// with a run read backwards gives the mirrored WENO(-) correction: a mirrored
-// window's differences are the negated forward ones, and the correction is odd
-// in the differences (beta and the weights are even, the numerator is linear).
+// WENO5 correction of K consecutive windows along a line, from scaled first
+// differences (two streams as float2 pairs).  With v the values whose
+// reconstruction is wanted, D_k their first differences and t_r, s_r the
+// second differences and beta parts of the weno5 comment, the correction of a
+// window to its centre value c is
+//   sum_r omega_r v^(r) - c = (D2 + 2 D3)/6 + (w0 (t1 - t0) - 2 w2 (t1 - t2)) / (6 sum w).
+// p holds Dt = D / 3, so that the run returns twice the correction (the
+// doubled split fluxes of the callers):
+//   2 (sum_r omega_r v^(r) - c) = Ft + (w0 (tt1 - tt0) - 2 w2 (tt1 - tt2)) / sum w,
+//   Ft = Dt2 + 2 Dt3,  tt = t / 3,
+// and (13/3) tt_r^2 + st_r^2 = (4/9) beta_r (st = s / 3), so
+// G_r = (13/3) tt_r^2 + st_r^2 + Geps with Geps = (4/9) eps is (4/9)(beta_r + eps),
+// and the weights w_r = d_r / G_r^2 up to a common factor are formed as
+// (3 g1 g2, 6 g0 g2, g0 g1) with g = G^2 (d = (3, 6, 1) / 10).  Window m takes
+// Dt1..Dt4 = p[m s] .. p[(m + 3) s] and writes to out[m os]; each window loads
+// one new difference, and its -2 (tt1 - tt2) is twice the previous window's
+// (tt1 - tt0), carried.  A mirrored window is the same run over the negated
+// differences read backwards (the caller stores them negated).
 template <int K>
-__device__ __forceinline__ void weno5d_slide2(const float2 *p, int s, float eps_, float sign, float2 *out, int os)
+__device__ __forceinline__ void weno5d_slide2(const float2 *p, int s, float Geps_, float2 *out, int os)
 {
-    const float2 k13 = bc2((float)(13.0 / 12.0)), q = bc2(0.25f), eps = bc2(eps_), six = bc2(6.0f * sign);
+    const float2 k = bc2((float)(13.0 / 3.0)), Geps = bc2(Geps_);
     float2 D1 = *p, D2 = *(p += s), D3 = *(p += s);
     float2 t1 = sub2(D3, D2), t2 = sub2(D2, D1);
-    float2 A1 = fma2(mul2(k13, t1), t1, eps), A2 = fma2(mul2(k13, t2), t2, eps);
+    float2 A1 = fma2(mul2(k, t1), t1, Geps), A2 = fma2(mul2(k, t2), t2, Geps);
+    float2 h = mul2(bc2(-2.0f), sub2(t1, t2));
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         const float2 D4 = *(p += s);
         const float2 t0 = sub2(D4, D3);
-        const float2 A0 = fma2(mul2(k13, t0), t0, eps);
+        const float2 A0 = fma2(mul2(k, t0), t0, Geps);
         const float2 s0 = fma2(bc2(-3.0f), D3, D4), s1 = add2(D2, D3), s2 = fma2(bc2(-3.0f), D2, D1);
-        float2 g0 = fma2(mul2(q, s0), s0, A0), g1 = fma2(mul2(q, s1), s1, A1), g2 = fma2(mul2(q, s2), s2, A2);
+        float2 g0 = fma2(s0, s0, A0), g1 = fma2(s1, s1, A1), g2 = fma2(s2, s2, A2);
         g0 = mul2(g0, g0);
         g1 = mul2(g1, g1);
         g2 = mul2(g2, g2);
-        const float2 w0 = mul2(bc2(0.3f), mul2(g1, g2)), w1 = mul2(bc2(0.6f), mul2(g0, g2)),
-                     w2 = mul2(bc2(0.1f), mul2(g0, g1));
-        const float2 sw = add2(add2(w0, w1), w2);
-        const float2 num =
-            fma2(w0, sub2(t1, t0), fma2(mul2(bc2(-2.0f), w2), sub2(t1, t2), mul2(fma2(bc2(2.0f), D3, D2), sw)));
-        const float2 den = mul2(six, sw);
-        *out = mul2(num, make_float2(fast_rcp(den.x), fast_rcp(den.y)));
+        const float2 w0 = mul2(g1, g2), w1 = mul2(g0, g2), w2 = mul2(g0, g1);  // times 3, 6, 1
+        const float2 sw = fma2(bc2(3.0f), w0, fma2(bc2(6.0f), w1, w2));
+        const float2 e0 = sub2(t1, t0);
+        const float2 num = fma2(w0, mul2(bc2(3.0f), e0), mul2(w2, h));
+        const float2 F = fma2(bc2(2.0f), D3, D2);
+        *out = fma2(num, make_float2(fast_rcp(sw.x), fast_rcp(sw.y)), F);
         out += os;
+        h = add2(e0, e0);
         D1 = D2;
         D2 = D3;
         D3 = D4;
