@@ -30,6 +30,7 @@ struct weno_ctx {
     double *S1 = nullptr, *S2 = nullptr, *Udev = nullptr;
     void *acc = nullptr;
     double *partials = nullptr, *sums_dev = nullptr;
+    double *bcs_dev = nullptr;  // weno_params.bc_state in device memory
     int nblocks_sum = 0;
     wg::Ctl *ctl = nullptr;
     wg::Ctl *ctl_host = nullptr;  // pinned mirror for reads

@@ -142,7 +142,51 @@ __device__ __forceinline__ void pair_diff2(const float4 ha, const float4 la, con
     dm_out[3] = fma2(al6, dE, make_float2(-FE.x, -FE.y));
 }
 
-template <int EPI, bool PD>
+// A point's FP32 hi/lo state in a tile that touches the boundary: the
+// boundary rule on the ghost indices (Sec. 4.5).  Kept out of line, so the
+// interior tiles' straight loads are not interleaved with this code.
+struct PointHL {
+    float4 h, l;
+};
+
+__device__ __noinline__ PointHL load_point_bc(const double *U, const float2 *hl, const float *din, long long N,
+                                              int nx, int ny, int bx0, int bx1, int by0, int by1,
+                                              const double *bcs, bool from_hl, int cx, int cy)
+{
+    PointHL p;
+    bool fx_ = false, fy_ = false;
+    int inx, iny;
+    cx = cx < nx + 2 ? cx : nx + 2;
+    cy = cy < ny + 2 ? cy : ny + 2;
+    cx = ghost_map(cx, nx, bx0, bx1, fx_, inx);
+    cy = ghost_map(cy, ny, by0, by1, fy_, iny);
+    if (inx >= 0 || iny >= 0) {  // a ghost of an inflow side holds the given state
+        const double *st = bcs + (inx >= 0 ? inx * 5 : (2 + iny) * 5);
+        split_f64(st[0], p.h.x, p.l.x);
+        split_f64(st[1], p.h.y, p.l.y);
+        split_f64(st[2], p.h.z, p.l.z);
+        split_f64(st[3], p.h.w, p.l.w);
+        return p;
+    }
+    const long long src = (long long)cy * nx + cx;
+    if (from_hl) {
+        const float2 q0 = hl[src], q1 = hl[N + src], q2 = hl[2 * N + src], q3 = hl[3 * N + src];
+        const float d0 = din[src], d1 = din[N + src], d2 = din[2 * N + src], d3 = din[3 * N + src];
+        p.h = make_float4(q0.x, q1.x, q2.x, q3.x);
+        p.l = make_float4(q0.y + d0, q1.y + d1, q2.y + d2, q3.y + d3);
+    } else {
+        split_f64(U[src], p.h.x, p.l.x);
+        split_f64(U[N + src], p.h.y, p.l.y);
+        split_f64(U[2 * N + src], p.h.z, p.l.z);
+        split_f64(U[3 * N + src], p.h.w, p.l.w);
+    }
+    if (fx_) { p.h.y = -p.h.y; p.l.y = -p.l.y; }
+    if (fy_) { p.h.z = -p.h.z; p.l.z = -p.l.z; }
+    return p;
+}
+
+// ST: the stage (0, 1, 2) of EPI_STAGE; EPI_RHS reads U like stage 0.
+template <int EPI, bool PD, int ST>
 __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 {
     using namespace xy2;
@@ -160,7 +204,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     const double dt = __longlong_as_double(dtbits);
     __shared__ float s_bdt;
     if (EPI == EPI_STAGE && threadIdx.x == 0)
-        s_bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+        s_bdt = f64_to_f32((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
     const float alY = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha);
@@ -173,8 +217,8 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     const bool own = gx < nx && gy < ny;
     const long long cell = (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
     // stage 1 reads U^n as FP64; stages 2 and 3 read the stored split and Delta_{k-1}
-    const bool from_hl = EPI == EPI_STAGE && a.stage > 0;
-    if (EPI == EPI_STAGE && a.stage == 2) {  // U^n at the own cell, for U^{n+1} = U^n + Delta_3
+    constexpr bool from_hl = EPI == EPI_STAGE && ST > 0;
+    if (EPI == EPI_STAGE && ST == 2) {  // U^n at the own cell, for U^{n+1} = U^n + Delta_3
 #pragma unroll
         for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + cell));
     }
@@ -182,25 +226,15 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     // ---- phase A: a point's FP32 hi/lo state, boundary rule on ghost indices
     auto load_point = [&](int lx, int ly, float4 &h, float4 &l) {
-        int cx = x0 + lx, cy = y0 + ly;
-        bool fx_ = false, fy_ = false;
         if (!interior) {
-            int inx, iny;
-            cx = cx < nx + 2 ? cx : nx + 2;
-            cy = cy < ny + 2 ? cy : ny + 2;
-            cx = ghost_map(cx, nx, a.bc[0][0], a.bc[0][1], fx_, inx);
-            cy = ghost_map(cy, ny, a.bc[1][0], a.bc[1][1], fy_, iny);
-            if (inx >= 0 || iny >= 0) {  // a ghost of an inflow side holds the given state
-                const double *st = inx >= 0 ? a.bc_state[0][inx] : a.bc_state[1][iny];
-                split_f64(st[0], h.x, l.x);
-                split_f64(st[1], h.y, l.y);
-                split_f64(st[2], h.z, l.z);
-                split_f64(st[3], h.w, l.w);
-                return;
-            }
+            const PointHL p = load_point_bc(a.U, a.hl, a.din, N, nx, ny, a.bc[0][0], a.bc[0][1], a.bc[1][0],
+                                            a.bc[1][1], a.bcs, from_hl, x0 + lx, y0 + ly);
+            h = p.h;
+            l = p.l;
+            return;
         }
-        const long long src = (long long)cy * nx + cx;
-        if (from_hl) {
+        const long long src = (long long)(y0 + ly) * nx + (x0 + lx);
+        if constexpr (from_hl) {
             const float2 *hl = a.hl + src;
             const float *d = a.din + src;
             const float2 q0 = __ldg(hl), q1 = __ldg(hl + N), q2 = __ldg(hl + 2 * N), q3 = __ldg(hl + 3 * N);
@@ -214,8 +248,6 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
             split_f64(__ldg(u + 2 * N), h.z, l.z);
             split_f64(__ldg(u + 3 * N), h.w, l.w);
         }
-        if (fx_) { h.y = -h.y; l.y = -l.y; }
-        if (fy_) { h.z = -h.z; l.z = -l.z; }
     };
 
     // the own point and the halo point of this thread: both loads go out
@@ -247,7 +279,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         float4 h, l, h2, l2;
         load_point(tx, ty, h, l);
         if (halo) load_point(hx, hy, h2, l2);
-        if (EPI == EPI_STAGE && a.stage == 0 && own) {  // the split of U^n, read by stages 2 and 3
+        if (EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
             a.hl[cell] = make_float2(h.x, l.x);
             a.hl[N + cell] = make_float2(h.y, l.y);
             a.hl[2 * N + cell] = make_float2(h.z, l.z);
@@ -316,7 +348,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             hn[f] = a.hl[f * N + cell].x;  // stage 1 wrote it in phase A (a plain, coherent load)
-            if (a.stage > 0) dk[f] = __ldg(a.din + f * N + cell);
+            if (ST > 0) dk[f] = __ldg(a.din + f * N + cell);
         }
     }
 
@@ -393,13 +425,13 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     bool bad = false;
     if (own) {
         const float bdt = s_bdt;
-        const float cd = a.stage == 1 ? 0.25f : (float)(2.0 / 3.0);
+        const float cd = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
         float q[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             float d = bdt * r[f];
-            if (a.stage > 0) d = fmaf(cd, dk[f], d);
-            if (a.stage < 2) a.dout[f * N + cell] = d;
+            if (ST > 0) d = fmaf(cd, dk[f], d);
+            if (ST < 2) a.dout[f * N + cell] = d;
             else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
             q[f] = hn[f] + d;  // the new state in FP32, for the wavespeed
         }
@@ -413,25 +445,33 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
 }
 
-template <int EPI, bool PD>
+template <int EPI, bool PD, int ST>
 static cudaError_t launch_xy2_t(const SweepArgs &a, cudaStream_t s)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_xy2<EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_xy2<EPI, PD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)xy2::BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[0] + xy2::TX - 1) / xy2::TX), (unsigned)((a.n[1] + xy2::TY - 1) / xy2::TY), 1);
-    k_xy2<EPI, PD><<<grid, xy2::NT, xy2::BYTES, s>>>(a);
+    k_xy2<EPI, PD, ST><<<grid, xy2::NT, xy2::BYTES, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int EPI, bool PD>
+static cudaError_t launch_xy2_s(const SweepArgs &a, cudaStream_t s)
+{
+    if (EPI == EPI_RHS || a.stage == 0) return launch_xy2_t<EPI, PD, 0>(a, s);
+    if (a.stage == 1) return launch_xy2_t<EPI, PD, 1>(a, s);
+    return launch_xy2_t<EPI, PD, 2>(a, s);
 }
 
 cudaError_t launch_xy2(int epi, const SweepArgs &a, cudaStream_t s)
 {
-    if (epi == EPI_RHS) return a.per_dir ? launch_xy2_t<EPI_RHS, true>(a, s) : launch_xy2_t<EPI_RHS, false>(a, s);
-    if (epi == EPI_STAGE) return a.per_dir ? launch_xy2_t<EPI_STAGE, true>(a, s) : launch_xy2_t<EPI_STAGE, false>(a, s);
+    if (epi == EPI_RHS) return a.per_dir ? launch_xy2_s<EPI_RHS, true>(a, s) : launch_xy2_s<EPI_RHS, false>(a, s);
+    if (epi == EPI_STAGE) return a.per_dir ? launch_xy2_s<EPI_STAGE, true>(a, s) : launch_xy2_s<EPI_STAGE, false>(a, s);
     return cudaErrorInvalidValue;
 }
 

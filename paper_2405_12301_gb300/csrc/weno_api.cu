@@ -61,6 +61,7 @@ static void free_all(weno_ctx *h)
     cudaFree(h->acc);
     cudaFree(h->partials);
     cudaFree(h->sums_dev);
+    cudaFree(h->bcs_dev);
     cudaFree(h->ctl);
     cudaFree(h->xbuf);
     for (auto &g : h->xgraphs) {
@@ -163,7 +164,8 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
         h->nblocks_sum = sums_blocks(h->N);
         ok = alloc((void **)&h->S1, sb) && alloc((void **)&h->S2, sb) && alloc(&h->acc, ab) &&
              alloc((void **)&h->partials, sizeof(double) * (size_t)h->nblocks_sum * h->nf) &&
-             alloc((void **)&h->sums_dev, sizeof(double) * h->nf);
+             alloc((void **)&h->sums_dev, sizeof(double) * h->nf) &&
+             alloc((void **)&h->bcs_dev, sizeof(p.bc_state));
     }
     if (!ok) {
         free_all(h);
@@ -172,7 +174,9 @@ extern "C" int weno_init(weno_handle *out, const weno_grid *grid, const weno_par
     }
     Ctl c{};
     c.max_steps = LLONG_MAX;
-    if (cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+    if ((h->bcs_dev && cudaMemcpyAsync(h->bcs_dev, p.bc_state, sizeof(p.bc_state), cudaMemcpyHostToDevice,
+                                       h->stream) != cudaSuccess) ||
+        cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         free_all(h);
         delete h;
@@ -244,6 +248,7 @@ static SweepArgs base_args(weno_ctx *h)
     a.eps_f = (float)h->p.eps_weno;
     for (int d = 0; d < 3; ++d) a.inv_h_f[d] = (float)a.inv_h[d];
     a.acc = h->acc;
+    a.bcs = h->bcs_dev;
     // a scalar law has one wavespeed |f'(u)| for every direction
     a.per_dir = h->p.alpha_mode == WENO_ALPHA_PER_DIR && h->p.model == WENO_MODEL_EULER ? 1 : 0;
     return a;

@@ -29,6 +29,7 @@ struct SweepArgs {
     long long stride[3]; // 1, nx, nx * ny
     int bc[3][2];
     double bc_state[3][2][5];  // conserved state held by the ghosts of an inflow side
+    const double *bcs;   // the same in device memory ([3][2][5]), for out-of-line boundary loads
     double inv_h[3];
     double gamma;
     double eps;
