@@ -23,6 +23,7 @@
 // per stage, and in 2D the residual never leaves the SM.
 #include <type_traits>
 
+#include "bulk_load.cuh"
 #include "weno_dev.cuh"
 #include "weno_internal.h"
 
@@ -60,8 +61,11 @@ template <int D, bool BULK> struct Layout {
 }  // namespace xy
 
 // The FP32-bulk (3D plane) kernel is held to 48 registers so that 5 CTAs (40
-// warps) share an SM; its shared memory allows that many.
-template <int D, bool BULK, int EPI, bool PD>
+// warps) share an SM; its shared memory allows that many.  ST (FP32-bulk): the
+// stage, which selects where the stencil state comes from -- the split of U
+// (stage 1, L(U)) or the stored split of U^n plus Delta_k (stages 2 and 3, the
+// stage state of k_xy2.cu).
+template <int D, bool BULK, int EPI, bool PD, int ST = 0>
 __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 {
     using namespace xy;
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 
     // the stage combination needs U^n at this thread's cell: issue the loads now
     double un[NF];
-    if (EPI == EPI_STAGE && a.stage > 0) {
+    if (!BULK && EPI == EPI_STAGE && a.stage > 0) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
@@ -128,15 +132,38 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
         if (fy_) q[2] = -q[2];
     };
 
+    // FP32-bulk: a point's hi/lo state (boundary rule on ghost indices)
+    auto load_point_b = [&](int lx, int ly, float *h, float *l) {
+        int cx = x0 + lx, cy = y0 + ly;
+        bool fx_ = false, fy_ = false;
+        if (!interior) {
+            int inx, iny;
+            cx = cx < nx + 2 ? cx : nx + 2;
+            cy = cy < ny + 2 ? cy : ny + 2;
+            cx = ghost_map(cx, nx, a.bc[0][0], a.bc[0][1], fx_, inx);
+            cy = ghost_map(cy, ny, a.bc[1][0], a.bc[1][1], fy_, iny);
+            if (inx >= 0 || iny >= 0) {
+                bulk_state<NF>(inx >= 0 ? a.bc_state[0][inx] : a.bc_state[1][iny], h, l);
+                return;
+            }
+        }
+        bulk_point<NF, (ST > 0)>(a, zoff + (long long)cy * nx + cx, h, l);
+        if (fx_) { h[1] = -h[1]; l[1] = -l[1]; }
+        if (fy_) { h[2] = -h[2]; l[2] = -l[2]; }
+    };
+
     // ---- phase A+F: own point (x and y fluxes) and one halo point per thread;
     // their loads go out before the reference state's barrier, so their latency
     // overlaps warp 0's work on the reference
-    double uk[NF];                // U^(k) at the own cell, kept for the stage combination
-    load_point(tx, ty, uk);
+    double uk[NF];                // U^(k) at the own cell (FP64), kept for the stage combination
+    float hq[NF], lq[NF];         // the own point's hi/lo (FP32-bulk)
+    if constexpr (BULK) load_point_b(tx, ty, hq, lq);
+    else load_point(tx, ty, uk);
     const bool halo = threadIdx.x < NHALO;
     int hx = 0, hy = 0;
     bool hdirx = false;
     double qd[NF];
+    float hh[NF], lh[NF];
     if (halo) {
         int t = threadIdx.x;
         if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
@@ -150,18 +177,17 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
             hx = k < 3 ? k - 3 : TX + k - 3;
             hdirx = true;
         }
-        load_point(hx, hy, qd);
+        if constexpr (BULK) load_point_b(hx, hy, hh, lh);
+        else load_point(hx, hy, qd);
     }
 
     // ---- reference state of the tile (FP32-bulk): its first cell
     if (BULK) {
-        if (threadIdx.x < 32) {
-            const long long c0 = zoff + (long long)(y0 < ny ? y0 : ny - 1) * nx + (x0 < nx ? x0 : nx - 1);
-            double q[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
+        if (threadIdx.x < 32) {  // the tile's first cell is inside the grid
+            float h0[NF], l0[NF];
+            load_point_b(0, 0, h0, l0);
             RefState<D> r;
-            make_ref<D>(q, a.gm1_f, r);
+            make_ref_hl<D>(h0, l0, a.gm1_f, r);
             if (threadIdx.x == 0) ref = r;
         }
         __syncthreads();
@@ -203,8 +229,10 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
 
     {
         T q[NF];
-        if constexpr (BULK) diff_from_ref<D>(uk, ref, q);
-        else {
+        if constexpr (BULK) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = (hq[f] - ref.hi[f]) + (lq[f] - ref.lo[f]);
+        } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = uk[f];
         }
@@ -213,8 +241,10 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     }
     if (halo) {
         T q[NF];
-        if constexpr (BULK) diff_from_ref<D>(qd, ref, q);
-        else {
+        if constexpr (BULK) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = (hh[f] - ref.hi[f]) + (lh[f] - ref.lo[f]);
+        } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = qd[f];
         }
@@ -370,21 +400,31 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
     }
 }
 
-template <int D, bool BULK, int EPI, bool PD>
-static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
+template <int D, bool BULK, int EPI, bool PD, int ST>
+static cudaError_t launch_xy_st(const SweepArgs &a, cudaStream_t s)
 {
     using L = xy::Layout<D, BULK>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_xy<D, BULK, EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_xy<D, BULK, EPI, PD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)L::bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[0] + xy::TX - 1) / xy::TX), (unsigned)((a.n[1] + xy::TY - 1) / xy::TY),
               (unsigned)a.n[2]);
-    k_xy<D, BULK, EPI, PD><<<grid, xy::NT, L::bytes, s>>>(a);
+    k_xy<D, BULK, EPI, PD, ST><<<grid, xy::NT, L::bytes, s>>>(a);
     return cudaGetLastError();
+}
+
+// FP32-bulk: the stage selects the stencil-state source (a handle's stage
+// state exists only inside a step; L(U) reads U like stage 1)
+template <int D, bool BULK, int EPI, bool PD>
+static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
+{
+    if (!BULK || a.hl == nullptr || a.stage == 0) return launch_xy_st<D, BULK, EPI, PD, 0>(a, s);
+    if (a.stage == 1) return launch_xy_st<D, BULK, EPI, PD, 1>(a, s);
+    return launch_xy_st<D, BULK, EPI, PD, 2>(a, s);
 }
 
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)

@@ -2,6 +2,7 @@
 // residual of a stage (the x and y directions run in k_xy.cu).
 #include <type_traits>
 
+#include "bulk_load.cuh"
 #include "weno_dev.cuh"
 #include "weno_internal.h"
 
@@ -13,6 +14,9 @@ namespace wg {
 // its 32 columns.  Same phases as above for one direction; the epilogue adds
 // the x+y part left in the accumulator by k_xy<3, ..., EPI_STORE>, then writes
 // L(U) or applies the SSP-RK3 stage combination and publishes the wavespeed max.
+// FP32-bulk runs the stages on increments (the stage state of k_xy2.cu): stage
+// 1 stores the hi/lo split of U^n and Delta_1, stages 2 and 3 read them, and
+// only stage 3 touches FP64 (U^{n+1} = U^n + Delta_3); ST is the stage.
 namespace zs {
 constexpr int NT = 256;
 constexpr int TX = 32, TZ = 8;
@@ -31,7 +35,7 @@ template <bool BULK> struct Layout {
 };
 }  // namespace zs
 
-template <bool BULK, int EPI, bool PD>
+template <bool BULK, int EPI, bool PD, int ST = 0>
 __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
 {
     using namespace zs;
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     const long long cell = yoff + (long long)(gz < nz ? gz : nz - 1) * sz + (gx < nx ? gx : nx - 1);
 
     double un[NF];
-    if (EPI == EPI_STAGE && a.stage > 0) {
+    if (!BULK && EPI == EPI_STAGE && a.stage > 0) {
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
@@ -88,6 +92,23 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         for (int f = 0; f < NF; ++f) q[f] = __ldg(src + f * N);
         if (fz_) q[3] = -q[3];
     };
+    // FP32-bulk: a point's hi/lo state (boundary rule on ghost indices)
+    auto load_point_b = [&](int lx, int lz, float *h, float *l) {
+        int cx = x0 + lx, cz = z0 + lz;
+        bool fz_ = false;
+        if (!interior) {
+            int inz;
+            cx = cx < nx ? cx : nx - 1;
+            cz = cz < nz + 2 ? cz : nz + 2;
+            cz = ghost_map(cz, nz, a.bc[2][0], a.bc[2][1], fz_, inz);
+            if (inz >= 0) {
+                bulk_state<NF>(a.bc_state[2][inz], h, l);
+                return;
+            }
+        }
+        bulk_point<NF, (ST > 0)>(a, yoff + (long long)cz * sz + cx, h, l);
+        if (fz_) { h[3] = -h[3]; l[3] = -l[3]; }
+    };
     auto flux_store = [&](const T *q, int lx, int lz) {
         T fp[NF], fm[NF];
         if constexpr (BULK) split_flux_diff<3, 2, true>(q, ref, al, a.gm1_f, fp, fm);
@@ -103,20 +124,27 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     // own and halo loads go out before the reference state's barrier, so their
     // latency overlaps warp 0's work on the reference
     double uk[NF];
-    float hk[NF], lk[NF];
-    load_point(tx, tz, uk);
+    float hk[NF], lk[NF];  // FP32-bulk: the own point's hi/lo
+    if constexpr (BULK) load_point_b(tx, tz, hk, lk);
+    else load_point(tx, tz, uk);
     const bool halo = threadIdx.x < NHALO;
     const int hx = threadIdx.x & 31, hz = (threadIdx.x >> 5) < 3 ? (threadIdx.x >> 5) - 3 : TZ + (threadIdx.x >> 5) - 3;
     double qd[NF];
-    if (halo) load_point(hx, hz, qd);
-    if (BULK) {
-        if (threadIdx.x < 32) {
-            const long long c0 = yoff + (long long)(z0 < nz ? z0 : nz - 1) * sz + (x0 < nx ? x0 : nx - 1);
-            double q[NF];
+    float hh[NF], lh[NF];
+    if (halo) {
+        if constexpr (BULK) load_point_b(hx, hz, hh, lh);
+        else load_point(hx, hz, qd);
+    }
+    if (BULK && EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
 #pragma unroll
-            for (int f = 0; f < NF; ++f) q[f] = __ldg(a.U + f * N + c0);
+        for (int f = 0; f < NF; ++f) a.hl[f * N + cell] = make_float2(hk[f], lk[f]);
+    }
+    if (BULK) {
+        if (threadIdx.x < 32) {  // the tile's first cell is inside the grid
+            float h0[NF], l0[NF];
+            load_point_b(0, 0, h0, l0);
             RefState<3> r;
-            make_ref<3>(q, a.gm1_f, r);
+            make_ref_hl<3>(h0, l0, a.gm1_f, r);
             if (threadIdx.x == 0) ref = r;
         }
         __syncthreads();
@@ -125,10 +153,7 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         T q[NF];
         if constexpr (BULK) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                split_f64(uk[f], hk[f], lk[f]);
-                q[f] = (hk[f] - ref.hi[f]) + (lk[f] - ref.lo[f]);
-            }
+            for (int f = 0; f < NF; ++f) q[f] = (hk[f] - ref.hi[f]) + (lk[f] - ref.lo[f]);
         } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = uk[f];
@@ -138,8 +163,10 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     if (halo) {
         const int lx = hx, lz = hz;
         T q[NF];
-        if constexpr (BULK) diff_from_ref<3>(qd, ref, q);
-        else {
+        if constexpr (BULK) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) q[f] = (hh[f] - ref.hi[f]) + (lh[f] - ref.lo[f]);
+        } else {
 #pragma unroll
             for (int f = 0; f < NF; ++f) q[f] = qd[f];
         }
@@ -192,22 +219,20 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
         return;
     }
     if constexpr (BULK) {
+        // Delta_{k+1} = b_k (Delta_k + dt R); stage 3 ends the step with U^n + Delta_3
         float s = 0.0f, sd[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
         if (own) {
-            const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-            const float bdt = f64_to_f32((a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            const float bdt = f64_to_f32((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            const float cd = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
             float qn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                float dl = bdt * r[f];
-                if (a.stage > 0) {
-                    float hn, ln;
-                    split_f64(un[f], hn, ln);
-                    dl = fmaf(anf, (hn - hk[f]) + (ln - lk[f]), dl);
-                }
-                a.Uout[f * N + cell] = uk[f] + (double)dl;
-                qn[f] = hk[f] + (lk[f] + dl);
+                float d = bdt * r[f];
+                if (ST > 0) d = fmaf(cd, __ldg(a.din + f * N + cell), d);
+                if (ST < 2) a.dout[f * N + cell] = d;
+                else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
+                qn[f] = hk[f] + d;  // the new state in FP32 (hk is the hi part of U^n)
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
             if (PD && !bad) dirspeeds_f32<3>(qn, a.gamma_f, sd);
@@ -241,20 +266,28 @@ __global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
     }
 }
 
-template <bool BULK, int EPI, bool PD>
-static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
+template <bool BULK, int EPI, bool PD, int ST>
+static cudaError_t launch_z_st(const SweepArgs &a, cudaStream_t s)
 {
     using L = zs::Layout<BULK>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI, PD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)L::bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ), (unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1]);
-    k_z<BULK, EPI, PD><<<grid, zs::NT, L::bytes, s>>>(a);
+    k_z<BULK, EPI, PD, ST><<<grid, zs::NT, L::bytes, s>>>(a);
     return cudaGetLastError();
+}
+
+template <bool BULK, int EPI, bool PD>
+static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
+{
+    if (!BULK || EPI != EPI_STAGE || a.stage == 0) return launch_z_st<BULK, EPI, PD, 0>(a, s);
+    if (a.stage == 1) return launch_z_st<BULK, EPI, PD, 1>(a, s);
+    return launch_z_st<BULK, EPI, PD, 2>(a, s);
 }
 
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s)

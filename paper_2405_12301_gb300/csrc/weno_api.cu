@@ -285,8 +285,8 @@ static int enqueue_step(weno_ctx *h, double *U, cudaStream_t s)
     CK(h, launch(h, 7, s, [&] { return launch_step_begin(h->ctl, s); }));
     double *in[3] = {U, h->S1, h->S2};
     double *outs[3] = {h->S1, h->S2, U};
-    // 2D FP32-bulk keeps the split of U^n in S1 and the FP32 increments in S2
-    const bool inc = h->dim == 2 && bulk(h) && h->p.model == WENO_MODEL_EULER;
+    // FP32-bulk (2D and 3D) keeps the split of U^n in S1 and the FP32 increments in S2
+    const bool inc = h->dim >= 2 && bulk(h) && h->p.model == WENO_MODEL_EULER;
     float *delta[2] = {reinterpret_cast<float *>(h->S2), reinterpret_cast<float *>(h->S2) + h->nf * h->N};
     for (int k = 0; k < 3; ++k) {
         SweepArgs a = base_args(h);

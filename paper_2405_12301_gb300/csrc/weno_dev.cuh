@@ -358,6 +358,31 @@ template <int D> struct RefState {
     float rho, m[D], u[D], H;  // H = rho E + p
 };
 
+// The same from a state already split into FP32 hi + lo (lo may carry a stage
+// increment, far above FP32 rounding, so the primitives take hi + lo).
+template <int D>
+__device__ __forceinline__ void make_ref_hl(const float *h, const float *l, float gm1, RefState<D> &r)
+{
+    float q[D + 2];
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) {
+        r.hi[f] = h[f];
+        r.lo[f] = l[f];
+        q[f] = h[f] + l[f];
+    }
+    r.rho = q[0];
+    const float ir = 1.0f / r.rho;
+    float ke = 0.0f;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        r.m[e] = q[1 + e];
+        r.u[e] = r.m[e] * ir;
+        ke += r.m[e] * r.u[e];
+    }
+    const float p = gm1 * (q[D + 1] - 0.5f * ke);
+    r.H = q[D + 1] + p;
+}
+
 template <int D>
 __device__ __forceinline__ void make_ref(const double *q, float gm1, RefState<D> &r)
 {
