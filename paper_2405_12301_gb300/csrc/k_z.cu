@@ -36,7 +36,7 @@ template <bool BULK> struct Layout {
 }  // namespace zs
 
 template <bool BULK, int EPI, bool PD, int ST = 0>
-__global__ void __launch_bounds__(zs::NT) k_z(const SweepArgs a)
+__global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
 {
     using namespace zs;
     using L = Layout<BULK>;
