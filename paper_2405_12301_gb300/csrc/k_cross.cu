@@ -274,16 +274,25 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
                                 for (int k = 0; k < 7; ++k) acc[k] += lx * C[(f * CP + ii + k) * CS + x];
                             }
                         } else {
+                            // f32x2: even and odd entries accumulate in the two lanes (one issue
+                            // slot per two FMAs), summed at the end
+                            float2 a2[7], ra2 = bc2(0.0f);
+#pragma unroll
+                            for (int k = 0; k < 7; ++k) a2[k] = bc2(0.0f);
                             for (int x = 0; x < cl4; x += 4) {
                                 const float4 l4 = *reinterpret_cast<const float4 *>(lv + x);
+                                const float2 lxy = make_float2(l4.x, l4.y), lzw = make_float2(l4.z, l4.w);
 #pragma unroll
                                 for (int k = 0; k < 7; ++k) {
                                     const float4 c4 = *reinterpret_cast<const float4 *>(C + (f * CP + ii + k) * CS + x);
-                                    acc[k] = fmaf(l4.x, c4.x, fmaf(l4.y, c4.y, fmaf(l4.z, c4.z, fmaf(l4.w, c4.w, acc[k]))));
+                                    a2[k] = fma2(lzw, make_float2(c4.z, c4.w), fma2(lxy, make_float2(c4.x, c4.y), a2[k]));
                                 }
                                 const float4 r4 = *reinterpret_cast<const float4 *>(Cref + f * CS + x);
-                                racc = fmaf(l4.x, r4.x, fmaf(l4.y, r4.y, fmaf(l4.z, r4.z, fmaf(l4.w, r4.w, racc))));
+                                ra2 = fma2(lzw, make_float2(r4.z, r4.w), fma2(lxy, make_float2(r4.x, r4.y), ra2));
                             }
+#pragma unroll
+                            for (int k = 0; k < 7; ++k) acc[k] = a2[k].x + a2[k].y;
+                            racc = ra2.x + ra2.y;
                         }
                         ctr[f] = racc;
 #pragma unroll
@@ -297,15 +306,21 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
 #pragma unroll
                                 for (int k = 0; k < 7; ++k) acc[k] += vv[k * 5 * VP + x] * cx;
                             }
-                        } else {
+                        } else {  // f32x2 even / odd partial sums, as above
+                            float2 a2[7];
+#pragma unroll
+                            for (int k = 0; k < 7; ++k) a2[k] = bc2(0.0f);
                             for (int x = 0; x < cl4; x += 4) {
                                 const float4 c4 = *reinterpret_cast<const float4 *>(crow + x);
+                                const float2 cxy = make_float2(c4.x, c4.y), czw = make_float2(c4.z, c4.w);
 #pragma unroll
                                 for (int k = 0; k < 7; ++k) {
                                     const float4 w4 = *reinterpret_cast<const float4 *>(vv + k * 5 * VP + x);
-                                    acc[k] = fmaf(w4.x, c4.x, fmaf(w4.y, c4.y, fmaf(w4.z, c4.z, fmaf(w4.w, c4.w, acc[k]))));
+                                    a2[k] = fma2(make_float2(w4.z, w4.w), czw, fma2(make_float2(w4.x, w4.y), cxy, a2[k]));
                                 }
                             }
+#pragma unroll
+                            for (int k = 0; k < 7; ++k) acc[k] = a2[k].x + a2[k].y;
                         }
                         ctr[f] = acc[3];
 #pragma unroll

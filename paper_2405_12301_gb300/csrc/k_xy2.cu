@@ -211,68 +211,17 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     const int nx = a.n[0], ny = a.n[1];
     const long long N = a.N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    // stage 1 reads U^n as FP64; stages 2 and 3 read the stored split and Delta_{k-1}
-    constexpr bool from_hl = EPI == EPI_STAGE && ST > 0;
-    const float2 al = make_float2(alX * (float)(1.0 / 6.0), alY * (float)(1.0 / 6.0));
-    const float gm1 = a.gm1_f;
-
-    // persistent: tiles blockIdx.x, blockIdx.x + gridDim.x, ... in row-major
-    // order, so the CTAs resident at a time cover a band of neighbouring tiles
-    // (shared halos in L2); each tile prefetches the next one's own cells into
-    // L2, and the wavespeed max is published once per CTA
-    const int nbx = (nx + TX - 1) / TX, ntiles = nbx * ((ny + TY - 1) / TY);
-    // the CTA's wavespeed maxima (bit patterns of non-negative floats) and its
-    // non-physical flag, kept in shared memory rather than in registers
-    __shared__ unsigned s_max[3];
-    __shared__ int s_bad;
-    if (threadIdx.x < 3) s_max[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) s_bad = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int x0 = (tile % nbx) * TX, y0 = (tile / nbx) * TY;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
     const long long cell = (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
-    {
-        const int nt = tile + (int)gridDim.x;
-        if (nt < ntiles) {
-            const int nxg = (nt % nbx) * TX + tx, nyg = (nt / nbx) * TY + ty;
-            const long long nc = (long long)(nyg < ny ? nyg : ny - 1) * nx + (nxg < nx ? nxg : nx - 1);
+    // stage 1 reads U^n as FP64; stages 2 and 3 read the stored split and Delta_{k-1}
+    constexpr bool from_hl = EPI == EPI_STAGE && ST > 0;
+    if (EPI == EPI_STAGE && ST == 2) {  // U^n at the own cell, for U^{n+1} = U^n + Delta_3
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                if (from_hl) {
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hl + f * N + nc));
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.din + f * N + nc));
-                }
-                if (!from_hl || ST == 2) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + nc));
-            }
-        }
+        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + cell));
     }
-    // the halo point of this thread and the pair it starts (formed per tile: cheaper than holding it)
-    const bool halo = threadIdx.x < NHALO;
-    int hk = 0, hslot = 0, bslot = 0, hx = 0, hy = 0;
-    bool hdirx = false;
-    if (halo) {
-        int t = threadIdx.x;
-        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
-            hx = t & 31;
-            hk = t >> 5;
-            hy = hk < 3 ? hk - 3 : TY + hk - 3;
-            hslot = YH0 + hk * TX + hx;
-            // its upper pair, except from the last row; row -1's upper point is own row 0
-            bslot = hk == 2 ? own_slot(hx, 0) : YH0 + (hk + 1) * TX + hx;
-        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
-            t -= NHY;
-            hy = t / 6;
-            hk = t - hy * 6;
-            hx = hk < 3 ? hk - 3 : TX + hk - 3;
-            hdirx = true;
-            hslot = XH0 + hy * 6 + hk;
-            bslot = hk == 2 ? own_slot(0, hy) : XH0 + hy * 6 + hk + 1;
-        }
-    }
-    const bool hpair = halo && hk != 5;
-
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
 
     // ---- phase A: a point's FP32 hi/lo state, boundary rule on ghost indices
@@ -303,6 +252,29 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     // the own point and the halo point of this thread: both loads go out
     // before either is stored, so their latencies overlap
+    const bool halo = threadIdx.x < NHALO;
+    int hk = 0, hslot = 0, bslot = 0, hx = 0, hy = 0;
+    bool hdirx = false;
+    if (halo) {
+        int t = threadIdx.x;
+        if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
+            hx = t & 31;
+            hk = t >> 5;
+            hy = hk < 3 ? hk - 3 : TY + hk - 3;
+            hslot = YH0 + hk * TX + hx;
+            // its upper pair, except from the last row; row -1's upper point is own row 0
+            bslot = hk == 2 ? own_slot(hx, 0) : YH0 + (hk + 1) * TX + hx;
+        } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
+            t -= NHY;
+            hy = t / 6;
+            hk = t - hy * 6;
+            hx = hk < 3 ? hk - 3 : TX + hk - 3;
+            hdirx = true;
+            hslot = XH0 + hy * 6 + hk;
+            bslot = hk == 2 ? own_slot(0, hy) : XH0 + hy * 6 + hk + 1;
+        }
+    }
+    const bool hpair = halo && hk != 5;
     {
         float4 h, l, h2, l2;
         load_point(tx, ty, h, l);
@@ -323,6 +295,8 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     __syncthreads();
 
     // ---- phase F: neighbour-pair differences
+    const float2 al = make_float2(alX * (float)(1.0 / 6.0), alY * (float)(1.0 / 6.0));
+    const float gm1 = a.gm1_f;
     {
         const int sa = own_slot(tx, ty);
         const int sbx = tx + 1 < TX ? own_slot(tx + 1, ty) : xh_slot(TX, ty);
@@ -444,9 +418,12 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 #pragma unroll
             for (int f = 0; f < NF; ++f) a.Rout[f * N + cell] = f32_to_f64(r[f]);
         }
+        return;
     }
-    float sp = 0.0f, sd[2] = {0.0f, 0.0f};
-    if (EPI == EPI_STAGE && own) {  // Delta_{k+1} = b_k (Delta_k + dt R); stage 3 ends the step
+    // EPI_STAGE: Delta_{k+1} = b_k (Delta_k + dt R); stage 3 ends the step
+    float s = 0.0f, sd[2] = {0.0f, 0.0f};
+    bool bad = false;
+    if (own) {
         const float bdt = s_bdt;
         const float cd = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
         float q[NF];
@@ -458,36 +435,13 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
             else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
             q[f] = hn[f] + d;  // the new state in FP32, for the wavespeed
         }
-        bool b;
-        sp = wavespeed_f32<2>(q, a.gamma_f, b);
-        if (b) s_bad = 1;
-        if (PD && !b) dirspeeds_f32<2>(q, a.gamma_f, sd);
+        s = wavespeed_f32<2>(q, a.gamma_f, bad);
+        if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);
     }
-    if (EPI == EPI_STAGE) {  // warp maxima, then one shared atomic per warp
-        const unsigned m0 = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(sp));
-        if ((threadIdx.x & 31) == 0) atomicMax(&s_max[0], m0);
-        if (PD) {
-            const unsigned m1 = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(sd[0]));
-            const unsigned m2 = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(sd[1]));
-            if ((threadIdx.x & 31) == 0) {
-                atomicMax(&s_max[1], m1);
-                atomicMax(&s_max[2], m2);
-            }
-        }
-    }
-    __syncthreads();  // the next tile's points overwrite this tile's faces
-    }  // tiles
-    if (EPI == EPI_STAGE && threadIdx.x == 0) {  // one atomic per CTA and slot, on the FP64 bit pattern
-        if (s_max[0]) atomicMax(&a.ctl->alpha[a.slot_out],
-                                (unsigned long long)__double_as_longlong(f32_to_f64(__uint_as_float(s_max[0]))));
-        if (PD) {
+    block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
+    if constexpr (PD) {
 #pragma unroll
-            for (int e = 0; e < 2; ++e)
-                if (s_max[1 + e])
-                    atomicMax(&a.ctl->alpha_dir[a.slot_out][e],
-                              (unsigned long long)__double_as_longlong(f32_to_f64(__uint_as_float(s_max[1 + e]))));
-        }
-        if (s_bad) atomicOr(&a.ctl->status, ST_NONPHYSICAL);
+        for (int e = 0; e < 2; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
     }
 }
 
@@ -501,15 +455,8 @@ static cudaError_t launch_xy2_t(const SweepArgs &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xy2<EPI, PD, ST>, xy2::NT, xy2::BYTES);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
-    }
-    const long long tiles = (long long)((a.n[0] + xy2::TX - 1) / xy2::TX) * ((a.n[1] + xy2::TY - 1) / xy2::TY);
-    const long long cap = (long long)sm_count() * per_sm;
-    k_xy2<EPI, PD, ST><<<(unsigned)(tiles < cap ? tiles : cap), xy2::NT, xy2::BYTES, s>>>(a);
+    dim3 grid((unsigned)((a.n[0] + xy2::TX - 1) / xy2::TX), (unsigned)((a.n[1] + xy2::TY - 1) / xy2::TY), 1);
+    k_xy2<EPI, PD, ST><<<grid, xy2::NT, xy2::BYTES, s>>>(a);
     return cudaGetLastError();
 }
 
