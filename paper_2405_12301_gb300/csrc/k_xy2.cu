@@ -98,48 +98,47 @@ __device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1
     return P;
 }
 
-// Split-flux differences of two pairs at once: lane x the x pair (a, bx),
-// lane y the y pair (a, by).  Per lane the normal momentum is n (x: m_x,
-// y: m_y) and the other one t.  Outputs, per component in the lane's own order
-// (rho, n, t, E), are scaled for weno5d_slide2: dp = (f(+)(U_b) - f(+)(U_a)) / 3
-// and dm = -(f(-)(U_b) - f(-)(U_a)) / 3 (the mirrored WENO(-) runs read the
-// negated differences), formed as (F +/- alpha U) differences times 1/6.
-__device__ __forceinline__ void pair_diff2(const float4 ha, const float4 la, const Prim2 &A, const float4 hbx,
-                                           const float4 lbx, const float4 hby, const float4 lby, float2 al6,
-                                           float gm1, float2 *dp_out, float2 *dm_out)
+// Split-flux differences of one pair (a, b) along direction DIR (0: x, 1: y),
+// stored scaled for weno5d_slide2: dp = (f(+)(U_b) - f(+)(U_a)) / 3 and
+// dm = -(f(-)(U_b) - f(-)(U_a)) / 3 (the mirrored WENO(-) runs read the
+// negated differences), formed as (F +/- alpha U) differences times 1/6, as
+// component pairs (rho, m_x) and (m_y, E).  The hi/lo differences are taken
+// on those same pairs; the identities between them are scalar.  Every pair is
+// formed by this one function, so a pair shared by two CTAs (a tile edge) gets
+// bitwise the same differences in both.
+template <int DIR>
+__device__ __forceinline__ void pair_diff1(const float4 ha, const float4 la, const Prim2 &A, const float4 hb,
+                                           const float4 lb, float al6, float gm1, float2 *dp_out, float2 *dm_out)
 {
-    // dU = U_b - U_a from the hi/lo splits
-    const float2 dR = add2(sub2(make_float2(hbx.x, hby.x), bc2(ha.x)), sub2(make_float2(lbx.x, lby.x), bc2(la.x)));
-    const float2 dQ1 = add2(sub2(make_float2(hbx.y, hby.y), bc2(ha.y)), sub2(make_float2(lbx.y, lby.y), bc2(la.y)));
-    const float2 dQ2 = add2(sub2(make_float2(hbx.z, hby.z), bc2(ha.z)), sub2(make_float2(lbx.z, lby.z), bc2(la.z)));
-    const float2 dE = add2(sub2(make_float2(hbx.w, hby.w), bc2(ha.w)), sub2(make_float2(lbx.w, lby.w), bc2(la.w)));
-    const float2 dMn = make_float2(dQ1.x, dQ2.y), dMt = make_float2(dQ2.x, dQ1.y);
-    const float2 una = make_float2(A.u, A.v), uta = make_float2(A.v, A.u);
-    const float2 nuna = make_float2(-A.u, -A.v), nuta = make_float2(-A.v, -A.u);
-    const float2 mna = make_float2(A.mx, A.my), mta = make_float2(A.my, A.mx);
-    const float2 rb = add2(bc2(A.rho), dR);
-    const float2 irb = make_float2(fast_rcp(rb.x), fast_rcp(rb.y));
-    const float2 dun = mul2(fma2(nuna, dR, dMn), irb);  // du_n = (dm_n - u_n,a drho) / rho_b
-    const float2 dut = mul2(fma2(nuta, dR, dMt), irb);
-    const float2 unb = add2(una, dun), utb = add2(uta, dut);
-    const float2 kn = fma2(mna, dun, mul2(dMn, unb));  // d(m_n u_n)
-    const float2 dk = fma2(mta, dut, fma2(dMt, utb, kn));  // d(m . u)
-    const float2 dp = mul2(bc2(gm1), fma2(bc2(-0.5f), dk, dE));
-    const float2 dH = add2(dE, dp);
+    const float2 d01 = add2(sub2(make_float2(hb.x, hb.y), make_float2(ha.x, ha.y)),
+                            sub2(make_float2(lb.x, lb.y), make_float2(la.x, la.y)));
+    const float2 d23 = add2(sub2(make_float2(hb.z, hb.w), make_float2(ha.z, ha.w)),
+                            sub2(make_float2(lb.z, lb.w), make_float2(la.z, la.w)));
+    const float dR = d01.x, dE = d23.y;
+    const float dMn = DIR == 0 ? d01.y : d23.x, dMt = DIR == 0 ? d23.x : d01.y;
+    const float una = DIR == 0 ? A.u : A.v, uta = DIR == 0 ? A.v : A.u;
+    const float mna = DIR == 0 ? A.mx : A.my, mta = DIR == 0 ? A.my : A.mx;
+    const float irb = fast_rcp(__fadd_rn(A.rho, dR));
+    const float dun = __fmul_rn(__fmaf_rn(-una, dR, dMn), irb);  // du_n = (dm_n - u_n,a drho) / rho_b
+    const float dut = __fmul_rn(__fmaf_rn(-uta, dR, dMt), irb);
+    const float unb = __fadd_rn(una, dun), utb = __fadd_rn(uta, dut);
+    const float kn = __fmaf_rn(mna, dun, __fmul_rn(dMn, unb));          // d(m_n u_n)
+    const float dk = __fmaf_rn(mta, dut, __fmaf_rn(dMt, utb, kn));      // d(m . u)
+    const float dp = __fmul_rn(gm1, __fmaf_rn(-0.5f, dk, dE));
+    const float dH = __fadd_rn(dE, dp);
+    const float Fn = __fadd_rn(kn, dp);
+    const float Ft = __fmaf_rn(mta, dun, __fmul_rn(dMt, unb));
+    const float FE = __fmaf_rn(una, dH, __fmul_rn(dun, __fadd_rn(A.H, dH)));
+    // the fluxes in the component order (rho, m_x, m_y, E), times 1/6
     const float2 sixth = bc2((float)(1.0 / 6.0));
-    const float2 Fr = mul2(sixth, dMn);
-    const float2 Fn = mul2(sixth, add2(kn, dp));
-    const float2 Ft = mul2(sixth, fma2(mta, dun, mul2(dMt, unb)));
-    const float2 FE = mul2(sixth, fma2(una, dH, mul2(dun, add2(bc2(A.H), dH))));
+    const float2 F01 = mul2(sixth, make_float2(dMn, DIR == 0 ? Fn : Ft));
+    const float2 F23 = mul2(sixth, make_float2(DIR == 0 ? Ft : Fn, FE));
+    const float2 a6 = bc2(al6);
     // (F + alpha dU) / 6 and -(F - alpha dU) / 6 = alpha dU / 6 - F / 6
-    dp_out[0] = fma2(al6, dR, Fr);
-    dp_out[1] = fma2(al6, dMn, Fn);
-    dp_out[2] = fma2(al6, dMt, Ft);
-    dp_out[3] = fma2(al6, dE, FE);
-    dm_out[0] = fma2(al6, dR, make_float2(-Fr.x, -Fr.y));
-    dm_out[1] = fma2(al6, dMn, make_float2(-Fn.x, -Fn.y));
-    dm_out[2] = fma2(al6, dMt, make_float2(-Ft.x, -Ft.y));
-    dm_out[3] = fma2(al6, dE, make_float2(-FE.x, -FE.y));
+    dp_out[0] = fma2(a6, d01, F01);
+    dp_out[1] = fma2(a6, d23, F23);
+    dm_out[0] = fma2(a6, d01, make_float2(-F01.x, -F01.y));
+    dm_out[1] = fma2(a6, d23, make_float2(-F23.x, -F23.y));
 }
 
 // A point's FP32 hi/lo state in a tile that touches the boundary: the
@@ -295,7 +294,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     __syncthreads();
 
     // ---- phase F: neighbour-pair differences
-    const float2 al = make_float2(alX * (float)(1.0 / 6.0), alY * (float)(1.0 / 6.0));
+    const float alx6 = alX * (float)(1.0 / 6.0), aly6 = alY * (float)(1.0 / 6.0);
     const float gm1 = a.gm1_f;
     {
         const int sa = own_slot(tx, ty);
@@ -303,41 +302,46 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const int sby = ty + 1 < TY ? own_slot(tx, ty + 1) : yh_slot(tx, TY);
         const float4 ha = Ph[sa], la = Pl[sa];
         const Prim2 A = prim2(ha, la, gm1);
-        float2 dp[4], dm[4];
-        pair_diff2(ha, la, A, Ph[sbx], Pl[sbx], Ph[sby], Pl[sby], al, gm1, dp, dm);
-        // x pair (lane x: rho, m_x, m_y, E) at index tx + 3 of row ty
+        float2 dp[2], dm[2];
+        // x pair at index tx + 3 of row ty
+        pair_diff1<0>(ha, la, A, Ph[sbx], Pl[sbx], alx6, gm1, dp, dm);
         const int ix = ty * PXP + tx + 3;
-        Dx[0 * NDX + ix] = make_float2(dp[0].x, dp[1].x);
-        Dx[1 * NDX + ix] = make_float2(dp[2].x, dp[3].x);
-        Dx[2 * NDX + ix] = make_float2(dm[0].x, dm[1].x);
-        Dx[3 * NDX + ix] = make_float2(dm[2].x, dm[3].x);
-        // y pair (lane y: rho, m_y, m_x, E) at index ty + 3 of column tx
+        Dx[0 * NDX + ix] = dp[0];
+        Dx[1 * NDX + ix] = dp[1];
+        Dx[2 * NDX + ix] = dm[0];
+        Dx[3 * NDX + ix] = dm[1];
+        // y pair at index ty + 3 of column tx
+        pair_diff1<1>(ha, la, A, Ph[sby], Pl[sby], aly6, gm1, dp, dm);
         const int iy = (ty + 3) * TX + tx;
-        Dy[0 * NDY + iy] = make_float2(dp[0].y, dp[2].y);
-        Dy[1 * NDY + iy] = make_float2(dp[1].y, dp[3].y);
-        Dy[2 * NDY + iy] = make_float2(dm[0].y, dm[2].y);
-        Dy[3 * NDY + iy] = make_float2(dm[1].y, dm[3].y);
+        Dy[0 * NDY + iy] = dp[0];
+        Dy[1 * NDY + iy] = dp[1];
+        Dy[2 * NDY + iy] = dm[0];
+        Dy[3 * NDY + iy] = dm[1];
     }
     if (hpair) {
         const float4 ha = Ph[hslot], la = Pl[hslot], hb = Ph[bslot], lb = Pl[bslot];
         const Prim2 A = prim2(ha, la, gm1);
-        float2 dp[4], dm[4];
-        pair_diff2(ha, la, A, hb, lb, hb, lb, al, gm1, dp, dm);  // the pair's own lane is used
+        float2 dp[2], dm[2];
+        int o;
+        float2 *Dd;
+        int nd;
         if (hdirx) {
             const int hy = (threadIdx.x - NHY) / 6;
-            const int ix = hy * PXP + (hk < 3 ? hk : TX + hk);  // a col + 3
-            Dx[0 * NDX + ix] = make_float2(dp[0].x, dp[1].x);
-            Dx[1 * NDX + ix] = make_float2(dp[2].x, dp[3].x);
-            Dx[2 * NDX + ix] = make_float2(dm[0].x, dm[1].x);
-            Dx[3 * NDX + ix] = make_float2(dm[2].x, dm[3].x);
+            pair_diff1<0>(ha, la, A, hb, lb, alx6, gm1, dp, dm);
+            o = hy * PXP + (hk < 3 ? hk : TX + hk);  // a col + 3
+            Dd = Dx;
+            nd = NDX;
         } else {
             const int hx = threadIdx.x & 31;
-            const int iy = (hk < 3 ? hk : TY + hk) * TX + hx;  // (a row + 3) * TX + col
-            Dy[0 * NDY + iy] = make_float2(dp[0].y, dp[2].y);
-            Dy[1 * NDY + iy] = make_float2(dp[1].y, dp[3].y);
-            Dy[2 * NDY + iy] = make_float2(dm[0].y, dm[2].y);
-            Dy[3 * NDY + iy] = make_float2(dm[1].y, dm[3].y);
+            pair_diff1<1>(ha, la, A, hb, lb, aly6, gm1, dp, dm);
+            o = (hk < 3 ? hk : TY + hk) * TX + hx;  // (a row + 3) * TX + col
+            Dd = Dy;
+            nd = NDY;
         }
+        Dd[0 * nd + o] = dp[0];
+        Dd[1 * nd + o] = dp[1];
+        Dd[2 * nd + o] = dm[0];
+        Dd[3 * nd + o] = dm[1];
     }
     __syncthreads();
 
