@@ -186,8 +186,10 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
     // stage combination coefficients (Eq. tt-ssprk3): U' = a_n U^n + b_n (U^k + dt R)
     const double an = a.stage == 0 ? 0.0 : (a.stage == 1 ? 0.75 : 1.0 / 3.0);
     const double bn = a.stage == 0 ? 1.0 : (a.stage == 1 ? 0.25 : 2.0 / 3.0);
-    const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : 1.0f / 3.0f);
-    const float bdtf = BULK ? f64_to_f32(bn * dt) : 0.0f;
+    // FP32-bulk: a_n and b_n dt as hi + lo pairs (no systematic coefficient rounding)
+    const float anf = a.stage == 0 ? 0.0f : (a.stage == 1 ? 0.75f : (float)(1.0 / 3.0));
+    const float anf_lo = a.stage == 2 ? (float)(1.0 / 3.0 - (double)(float)(1.0 / 3.0)) : 0.0f;
+    const float2 bdtf = BULK ? f64_to_f32x2(bn * dt) : make_float2(0.0f, 0.0f);
     for (int u = threadIdx.x; u < W * S; u += NT) {
         int w, i;
         if (DIR == 0) { w = u / S; i = u - w * S; }
@@ -225,11 +227,12 @@ __global__ void __launch_bounds__(NT) k_sweep(const SweepArgs a)
                     if constexpr (BULK) {
                         float hk, lk;
                         split_f64(uk, hk, lk);
-                        float dlt = bdtf * r[f];
+                        float dlt = fmaf(bdtf.x, r[f], bdtf.y * r[f]);
                         if (a.stage > 0) {
                             float hn, ln;
                             split_f64(a.Un[f * N + cell], hn, ln);
-                            dlt = fmaf(anf, (hn - hk) + (ln - lk), dlt);
+                            const float x = (hn - hk) + (ln - lk);
+                            dlt = fmaf(anf, x, fmaf(anf_lo, x, dlt));
                         }
                         out[f] = uk + f32_to_f64(dlt);
                     } else {

@@ -59,15 +59,15 @@ constexpr int PXP = PX + 2;                   // their row pitch in float2 (odd:
 constexpr int PY = TY + 5;                    // y pairs per column: a = row -3..TY+1
 constexpr int NDX = PXP * TY;                 // one [sign][component pair] block of x differences
 constexpr int NDY = PY * TX;                  // one block of y differences
-constexpr int NFX = (TX + 1) * TY;            // x faces per block
-constexpr int NFY = TX * (TY + 1);            // y faces per block
-// shared memory: differences, then the points (phase A-F) or the faces (W-C)
+constexpr int NC = TX * TY;                   // cells per block of run outputs
+// shared memory: differences, then the points (phases A-F) or the runs'
+// per-cell outputs (W-C)
 constexpr size_t DX_OFF = 0;
 constexpr size_t DY_OFF = DX_OFF + sizeof(float2) * 4 * NDX;
 constexpr size_t R_OFF = DY_OFF + sizeof(float2) * 4 * NDY;
 constexpr size_t PTS_BYTES = sizeof(float4) * 2 * NPT;
-constexpr size_t FACE_BYTES = sizeof(float2) * 4 * (NFX + NFY);
-constexpr size_t BYTES = R_OFF + (PTS_BYTES > FACE_BYTES ? PTS_BYTES : FACE_BYTES);
+constexpr size_t CELL_BYTES = sizeof(float2) * 8 * NC;
+constexpr size_t BYTES = R_OFF + (PTS_BYTES > CELL_BYTES ? PTS_BYTES : CELL_BYTES);
 
 __device__ __forceinline__ int own_slot(int lx, int ly) { return ly * TX + lx; }
 __device__ __forceinline__ int xh_slot(int lx, int ly) { return XH0 + ly * 6 + (lx < 0 ? lx + 3 : lx - TX + 3); }
@@ -195,15 +195,15 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     float2 *Dy = reinterpret_cast<float2 *>(smem + DY_OFF);   // [sign][pair][PY][TX]
     float4 *Ph = reinterpret_cast<float4 *>(smem + R_OFF);    // [NPT] hi parts (phases A-F)
     float4 *Pl = Ph + NPT;                                    // [NPT] lo parts
-    float2 *Fx = reinterpret_cast<float2 *>(smem + R_OFF);    // [sign][pair][TY][TX+1] (phases W-C)
-    float2 *Fy = Fx + 4 * NFX;                                // [sign][pair][TY+1][TX]
+    float2 *Px = reinterpret_cast<float2 *>(smem + R_OFF);    // [sign][pair][TY][TX] (phases W-C)
+    float2 *Py = Px + 4 * NC;                                 // [sign][pair][TY][TX]
 
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
-    __shared__ float s_bdt;
+    __shared__ float2 s_bdt;  // b_k dt as an FP32 pair hi + lo
     if (EPI == EPI_STAGE && threadIdx.x == 0)
-        s_bdt = f64_to_f32((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+        s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
     const float alY = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha);
@@ -357,14 +357,15 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
 
     // ---- phase W: WENO corrections of every face (the points are dead now;
-    // the face arrays take their place).  One run of TY + 1 = 9 faces per
-    // thread, pair w & 1, sign (w >> 1) & 1:
-    //   warps 0-3, y: column `lane`, faces 0..8;
-    //   warps 4-7, x: row lane & 7, faces 8 s .. 8 s + 8 for s = lane >> 3
-    //   (neighbouring segments share one face and write the same value).
+    // the runs' per-cell outputs take their place).  One run of TY + 1 = 9
+    // faces per thread, pair w & 1, sign (w >> 1) & 1:
+    //   warps 0-3, y: column `lane`, faces 0..8, cells 0..7;
+    //   warps 4-7, x: row lane & 7, faces 8 s .. 8 s + 8, cells 8 s .. 8 s + 7
+    //   for s = lane >> 3.
     // Face j's WENO(+) window takes the pairs a = j-3..j (indices j..j+3), its
     // mirrored WENO(-) window the pairs a = j+1..j-2 read backwards (indices
-    // j+4..j+1).  The runs return twice the corrections (see weno5d_slide2).
+    // j+4..j+1).  Each run leaves a cell its pair's difference plus the change
+    // of the doubled correction across the cell (weno5d_cells2).
     {
         const float Geps = (float)(4.0 / 9.0) * a.eps_f;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
@@ -374,44 +375,37 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         int st, os;
         if (w < 4) {
             p = Dy + blk * NDY + lane;
-            out = Fy + blk * NFY + lane;
+            out = Py + blk * NC + lane;
             st = TX;
             os = TX;
         } else {
             const int ly = lane & 7, j0 = (lane >> 3) * 8;
             p = Dx + blk * NDX + ly * PXP + j0;
-            out = Fx + blk * NFX + ly * (TX + 1) + j0;
+            out = Px + blk * NC + ly * TX + j0;
             st = 1;
             os = 1;
         }
-        if (sg) {  // WENO(-): differences j0+12 .. j0+1, faces j0+8 .. j0
+        if (sg) {  // WENO(-): differences j0+12 .. j0+1, cells j0+7 .. j0
             p += 12 * st;
-            out += TY * os;
-            st = -st;
-            os = -os;
+            out += (TY - 1) * os;
+            weno5d_cells2<TY + 1, false>(p, -st, Geps, out, -os);
+        } else {
+            weno5d_cells2<TY + 1, true>(p, st, Geps, out, os);
         }
-        weno5d_slide2<TY + 1>(p, st, Geps, out, os);
     }
     __syncthreads();
 
-    // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y from the cell's
-    // pairs (a = i-1 for f(+), a = i for f(-)) and its faces' corrections:
-    // twice the flux difference is 6 (Dt(+) - Dt(-)) + the doubled corrections'
-    // differences (Dt(-) holds the negated f(-) difference), and the halving
-    // rides on 1/h
+    // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y: twice each
+    // flux difference is the sum of the two runs' parts of the cell, and the
+    // halving rides on 1/h
     float r[NF];
     {
         const float2 nihx = bc2(-0.5f * a.inv_h_f[0]), nihy = bc2(-0.5f * a.inv_h_f[1]);
+        const int c = ty * TX + tx;
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
-            const int dx = ty * PXP + tx + 2, fx = ty * (TX + 1) + tx;
-            const float2 sx = fma2(bc2(6.0f), sub2(Dx[pr * NDX + dx], Dx[(2 + pr) * NDX + dx + 1]),
-                                   add2(sub2(Fx[pr * NFX + fx + 1], Fx[pr * NFX + fx]),
-                                        sub2(Fx[(2 + pr) * NFX + fx + 1], Fx[(2 + pr) * NFX + fx])));
-            const int dy = (ty + 2) * TX + tx, fy = ty * TX + tx;
-            const float2 sy = fma2(bc2(6.0f), sub2(Dy[pr * NDY + dy], Dy[(2 + pr) * NDY + dy + TX]),
-                                   add2(sub2(Fy[pr * NFY + fy + TX], Fy[pr * NFY + fy]),
-                                        sub2(Fy[(2 + pr) * NFY + fy + TX], Fy[(2 + pr) * NFY + fy])));
+            const float2 sx = add2(Px[pr * NC + c], Px[(2 + pr) * NC + c]);
+            const float2 sy = add2(Py[pr * NC + c], Py[(2 + pr) * NC + c]);
             const float2 rr = fma2(sy, nihy, mul2(sx, nihx));
             r[2 * pr] = rr.x;
             r[2 * pr + 1] = rr.y;
@@ -428,13 +422,17 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     float s = 0.0f, sd[2] = {0.0f, 0.0f};
     bool bad = false;
     if (own) {
-        const float bdt = s_bdt;
-        const float cd = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
+        // Delta = b_k dt R + c_k Delta_k with b_k dt and c_k = 2/3 as hi + lo pairs
+        // (c_k = 1/4 is exact), so the coefficients carry no systematic rounding
+        const float2 bdt = s_bdt;
+        constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
+        constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
         float q[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            float d = bdt * r[f];
-            if (ST > 0) d = fmaf(cd, dk[f], d);
+            float t = bdt.y * r[f];
+            if (ST > 0) t = fmaf(c_hi, dk[f], fmaf(c_lo, dk[f], t));
+            const float d = fmaf(bdt.x, r[f], t);
             if (ST < 2) a.dout[f * N + cell] = d;
             else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
             q[f] = hn[f] + d;  // the new state in FP32, for the wavespeed

@@ -223,13 +223,19 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
         float s = 0.0f, sd[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
         if (own) {
-            const float bdt = f64_to_f32((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
-            const float cd = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
+            // b_k dt and c_k = 2/3 as hi + lo pairs: no systematic coefficient rounding
+            const float2 bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
+            constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
             float qn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                float d = bdt * r[f];
-                if (ST > 0) d = fmaf(cd, __ldg(a.din + f * N + cell), d);
+                float t = bdt.y * r[f];
+                if (ST > 0) {
+                    const float dkf = __ldg(a.din + f * N + cell);
+                    t = fmaf(c_hi, dkf, fmaf(c_lo, dkf, t));
+                }
+                const float d = fmaf(bdt.x, r[f], t);
                 if (ST < 2) a.dout[f * N + cell] = d;
                 else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
                 qn[f] = hk[f] + d;  // the new state in FP32 (hk is the hi part of U^n)

@@ -81,6 +81,15 @@ __device__ __forceinline__ float f64_to_f32(double x)
     return hi + lo;
 }
 
+// An FP64 coefficient as an unevaluated FP32 pair hi + lo (to about 2^-48
+// relative): multiplying by hi alone would bias every use the same way by up
+// to 2^-24, which over many time steps is a systematic error.
+__device__ __forceinline__ float2 f64_to_f32x2(double x)
+{
+    const float hi = f64_to_f32(x);
+    return make_float2(hi, f64_to_f32(x - f32_to_f64(hi)));
+}
+
 __device__ __forceinline__ float fast_rcp(float x)
 {
     float y;
@@ -302,6 +311,53 @@ __device__ __forceinline__ void weno5d_slide2(const float2 *p, int s, float Geps
         const float2 F = fma2(bc2(2.0f), D3, D2);
         *out = fma2(num, make_float2(fast_rcp(sw.x), fast_rcp(sw.y)), F);
         out += os;
+        h = add2(e0, e0);
+        D1 = D2;
+        D2 = D3;
+        D3 = D4;
+        t2 = t1;
+        t1 = t0;
+        A2 = A1;
+        A1 = A0;
+    }
+}
+
+// The same run, emitting per cell instead of per face: with C_m the run's
+// output for window m, cell m - 1 (between the faces of windows m - 1 and m)
+// receives 6 D2_m + (C_m - C_{m-1}) (FWD; D2_m the window's second
+// difference, the cell's own pair), or -6 D2_m + (C_{m-1} - C_m) for a run read
+// backwards (!FWD), K - 1 values to out[(m - 1) os].  Those are the parts of a
+// cell's doubled flux difference that one run contributes (k_xy2 phase C).
+template <int K, bool FWD>
+__device__ __forceinline__ void weno5d_cells2(const float2 *p, int s, float Geps_, float2 *out, int os)
+{
+    const float2 k = bc2((float)(13.0 / 3.0)), Geps = bc2(Geps_), six = bc2(FWD ? 6.0f : -6.0f);
+    float2 D1 = *p, D2 = *(p += s), D3 = *(p += s);
+    float2 t1 = sub2(D3, D2), t2 = sub2(D2, D1);
+    float2 A1 = fma2(mul2(k, t1), t1, Geps), A2 = fma2(mul2(k, t2), t2, Geps);
+    float2 h = mul2(bc2(-2.0f), sub2(t1, t2));
+    float2 Cp = bc2(0.0f);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        const float2 D4 = *(p += s);
+        const float2 t0 = sub2(D4, D3);
+        const float2 A0 = fma2(mul2(k, t0), t0, Geps);
+        const float2 s0 = fma2(bc2(-3.0f), D3, D4), s1 = add2(D2, D3), s2 = fma2(bc2(-3.0f), D2, D1);
+        float2 g0 = fma2(s0, s0, A0), g1 = fma2(s1, s1, A1), g2 = fma2(s2, s2, A2);
+        g0 = mul2(g0, g0);
+        g1 = mul2(g1, g1);
+        g2 = mul2(g2, g2);
+        const float2 w0 = mul2(g1, g2), w1 = mul2(g0, g2), w2 = mul2(g0, g1);
+        const float2 sw = fma2(bc2(3.0f), w0, fma2(bc2(6.0f), w1, w2));
+        const float2 e0 = sub2(t1, t0);
+        const float2 num = fma2(w0, mul2(bc2(3.0f), e0), mul2(w2, h));
+        const float2 F = fma2(bc2(2.0f), D3, D2);
+        const float2 C = fma2(num, make_float2(fast_rcp(sw.x), fast_rcp(sw.y)), F);
+        if (m > 0) {
+            *out = fma2(six, D2, FWD ? sub2(C, Cp) : sub2(Cp, C));
+            out += os;
+        }
+        Cp = C;
         h = add2(e0, e0);
         D1 = D2;
         D2 = D3;
