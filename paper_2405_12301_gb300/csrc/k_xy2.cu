@@ -108,7 +108,7 @@ __device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1
 // bitwise the same differences in both.
 template <int DIR>
 __device__ __forceinline__ void pair_diff1(const float4 ha, const float4 la, const Prim2 &A, const float4 hb,
-                                           const float4 lb, float al6, float gm1, float2 *dp_out, float2 *dm_out)
+                                           const float4 lb, float al, float gm1, float2 *dp_out, float2 *dm_out)
 {
     const float2 d01 = add2(sub2(make_float2(hb.x, hb.y), make_float2(ha.x, ha.y)),
                             sub2(make_float2(lb.x, lb.y), make_float2(la.x, la.y)));
@@ -129,16 +129,16 @@ __device__ __forceinline__ void pair_diff1(const float4 ha, const float4 la, con
     const float Fn = __fadd_rn(kn, dp);
     const float Ft = __fmaf_rn(mta, dun, __fmul_rn(dMt, unb));
     const float FE = __fmaf_rn(una, dH, __fmul_rn(dun, __fadd_rn(A.H, dH)));
-    // the fluxes in the component order (rho, m_x, m_y, E), times 1/6
-    const float2 sixth = bc2((float)(1.0 / 6.0));
-    const float2 F01 = mul2(sixth, make_float2(dMn, DIR == 0 ? Fn : Ft));
-    const float2 F23 = mul2(sixth, make_float2(DIR == 0 ? Ft : Fn, FE));
-    const float2 a6 = bc2(al6);
-    // (F + alpha dU) / 6 and -(F - alpha dU) / 6 = alpha dU / 6 - F / 6
-    dp_out[0] = fma2(a6, d01, F01);
-    dp_out[1] = fma2(a6, d23, F23);
-    dm_out[0] = fma2(a6, d01, make_float2(-F01.x, -F01.y));
-    dm_out[1] = fma2(a6, d23, make_float2(-F23.x, -F23.y));
+    // the fluxes in the component order (rho, m_x, m_y, E); (F + alpha dU) and
+    // -(F - alpha dU), then one multiply by fl(1/6) each, so that every stored
+    // difference carries the same scale (undone exactly in phase C)
+    const float2 F01 = make_float2(dMn, DIR == 0 ? Fn : Ft);
+    const float2 F23 = make_float2(DIR == 0 ? Ft : Fn, FE);
+    const float2 a2 = bc2(al), sixth = bc2((float)(1.0 / 6.0));
+    dp_out[0] = mul2(sixth, fma2(a2, d01, F01));
+    dp_out[1] = mul2(sixth, fma2(a2, d23, F23));
+    dm_out[0] = mul2(sixth, fma2(a2, d01, make_float2(-F01.x, -F01.y)));
+    dm_out[1] = mul2(sixth, fma2(a2, d23, make_float2(-F23.x, -F23.y)));
 }
 
 // A point's FP32 hi/lo state in a tile that touches the boundary: the
@@ -202,8 +202,16 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
     __shared__ float2 s_bdt;  // b_k dt as an FP32 pair hi + lo
-    if (EPI == EPI_STAGE && threadIdx.x == 0)
-        s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+    // the residual factors -1 / (2 h_d 6 fl(1/6)) as FP32 pairs: phase C's sums
+    // are twice the flux differences times 6 fl(1/6) (the differences' scale),
+    // and a single rounded factor would bias every residual the same way
+    __shared__ float2 s_ih[2];
+    if (threadIdx.x == 0) {
+        if (EPI == EPI_STAGE) s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+        const double six_fl = 6.0 * (double)(float)(1.0 / 6.0);
+        s_ih[0] = f64_to_f32x2(-0.5 * a.inv_h[0] / six_fl);
+        s_ih[1] = f64_to_f32x2(-0.5 * a.inv_h[1] / six_fl);
+    }
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
     const float alY = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha);
@@ -294,7 +302,6 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     __syncthreads();
 
     // ---- phase F: neighbour-pair differences
-    const float alx6 = alX * (float)(1.0 / 6.0), aly6 = alY * (float)(1.0 / 6.0);
     const float gm1 = a.gm1_f;
     {
         const int sa = own_slot(tx, ty);
@@ -304,14 +311,14 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const Prim2 A = prim2(ha, la, gm1);
         float2 dp[2], dm[2];
         // x pair at index tx + 3 of row ty
-        pair_diff1<0>(ha, la, A, Ph[sbx], Pl[sbx], alx6, gm1, dp, dm);
+        pair_diff1<0>(ha, la, A, Ph[sbx], Pl[sbx], alX, gm1, dp, dm);
         const int ix = ty * PXP + tx + 3;
         Dx[0 * NDX + ix] = dp[0];
         Dx[1 * NDX + ix] = dp[1];
         Dx[2 * NDX + ix] = dm[0];
         Dx[3 * NDX + ix] = dm[1];
         // y pair at index ty + 3 of column tx
-        pair_diff1<1>(ha, la, A, Ph[sby], Pl[sby], aly6, gm1, dp, dm);
+        pair_diff1<1>(ha, la, A, Ph[sby], Pl[sby], alY, gm1, dp, dm);
         const int iy = (ty + 3) * TX + tx;
         Dy[0 * NDY + iy] = dp[0];
         Dy[1 * NDY + iy] = dp[1];
@@ -327,13 +334,13 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         int nd;
         if (hdirx) {
             const int hy = (threadIdx.x - NHY) / 6;
-            pair_diff1<0>(ha, la, A, hb, lb, alx6, gm1, dp, dm);
+            pair_diff1<0>(ha, la, A, hb, lb, alX, gm1, dp, dm);
             o = hy * PXP + (hk < 3 ? hk : TX + hk);  // a col + 3
             Dd = Dx;
             nd = NDX;
         } else {
             const int hx = threadIdx.x & 31;
-            pair_diff1<1>(ha, la, A, hb, lb, aly6, gm1, dp, dm);
+            pair_diff1<1>(ha, la, A, hb, lb, alY, gm1, dp, dm);
             o = (hk < 3 ? hk : TY + hk) * TX + hx;  // (a row + 3) * TX + col
             Dd = Dy;
             nd = NDY;
@@ -395,18 +402,18 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
     __syncthreads();
 
-    // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y: twice each
-    // flux difference is the sum of the two runs' parts of the cell, and the
-    // halving rides on 1/h
+    // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y: the sum of the
+    // two runs' parts of the cell is 2 * 6 fl(1/6) times each flux difference,
+    // removed by the exact factor pairs s_ih
     float r[NF];
     {
-        const float2 nihx = bc2(-0.5f * a.inv_h_f[0]), nihy = bc2(-0.5f * a.inv_h_f[1]);
+        const float2 ihx = s_ih[0], ihy = s_ih[1];
         const int c = ty * TX + tx;
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
             const float2 sx = add2(Px[pr * NC + c], Px[(2 + pr) * NC + c]);
             const float2 sy = add2(Py[pr * NC + c], Py[(2 + pr) * NC + c]);
-            const float2 rr = fma2(sy, nihy, mul2(sx, nihx));
+            const float2 rr = fma2(sy, bc2(ihy.x), fma2(sy, bc2(ihy.y), fma2(sx, bc2(ihx.x), mul2(sx, bc2(ihx.y)))));
             r[2 * pr] = rr.x;
             r[2 * pr + 1] = rr.y;
         }
