@@ -99,10 +99,10 @@ __device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1
 }
 
 // Split-flux differences of one pair (a, b) along direction DIR (0: x, 1: y),
-// stored scaled for weno5d_slide2: dp = (f(+)(U_b) - f(+)(U_a)) / 3 and
-// dm = -(f(-)(U_b) - f(-)(U_a)) / 3 (the mirrored WENO(-) runs read the
-// negated differences), formed as (F +/- alpha U) differences times 1/6, as
-// component pairs (rho, m_x) and (m_y, E).  The hi/lo differences are taken
+// stored scaled by the exact factor 1/4 for the WENO runs: dp = (f(+)(U_b) -
+// f(+)(U_a)) / 4 and dm = -(f(-)(U_b) - f(-)(U_a)) / 4 (the mirrored WENO(-)
+// runs read the negated differences), formed as (F +/- alpha U) differences
+// times 1/8, as component pairs (rho, m_x) and (m_y, E).  The hi/lo differences are taken
 // on those same pairs; the identities between them are scalar.  Every pair is
 // formed by this one function, so a pair shared by two CTAs (a tile edge) gets
 // bitwise the same differences in both.
@@ -130,15 +130,16 @@ __device__ __forceinline__ void pair_diff1(const float4 ha, const float4 la, con
     const float Ft = __fmaf_rn(mta, dun, __fmul_rn(dMt, unb));
     const float FE = __fmaf_rn(una, dH, __fmul_rn(dun, __fadd_rn(A.H, dH)));
     // the fluxes in the component order (rho, m_x, m_y, E); (F + alpha dU) and
-    // -(F - alpha dU), then one multiply by fl(1/6) each, so that every stored
-    // difference carries the same scale (undone exactly in phase C)
+    // -(F - alpha dU), times the exact 1/8 (a power of two: an inexact scale such
+    // as fl(1/6) would multiply every residual by the same 1 + 3e-8, a
+    // systematic error that grows with the number of steps)
     const float2 F01 = make_float2(dMn, DIR == 0 ? Fn : Ft);
     const float2 F23 = make_float2(DIR == 0 ? Ft : Fn, FE);
-    const float2 a2 = bc2(al), sixth = bc2((float)(1.0 / 6.0));
-    dp_out[0] = mul2(sixth, fma2(a2, d01, F01));
-    dp_out[1] = mul2(sixth, fma2(a2, d23, F23));
-    dm_out[0] = mul2(sixth, fma2(a2, d01, make_float2(-F01.x, -F01.y)));
-    dm_out[1] = mul2(sixth, fma2(a2, d23, make_float2(-F23.x, -F23.y)));
+    const float2 a2 = bc2(al), eighth = bc2(0.125f);
+    dp_out[0] = mul2(eighth, fma2(a2, d01, F01));
+    dp_out[1] = mul2(eighth, fma2(a2, d23, F23));
+    dm_out[0] = mul2(eighth, fma2(a2, d01, make_float2(-F01.x, -F01.y)));
+    dm_out[1] = mul2(eighth, fma2(a2, d23, make_float2(-F23.x, -F23.y)));
 }
 
 // A point's FP32 hi/lo state in a tile that touches the boundary: the
@@ -202,15 +203,15 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     if (a.check_dt && dtbits == 0) return;
     const double dt = __longlong_as_double(dtbits);
     __shared__ float2 s_bdt;  // b_k dt as an FP32 pair hi + lo
-    // the residual factors -1 / (2 h_d 6 fl(1/6)) as FP32 pairs: phase C's sums
-    // are twice the flux differences times 6 fl(1/6) (the differences' scale),
-    // and a single rounded factor would bias every residual the same way
+    // the residual factors -(2/3) / h_d as FP32 pairs hi + lo: phase C's sums are
+    // 3/2 times the flux differences (the differences are stored as 1/4 of
+    // themselves, and the runs return 6/4 of the corrections), and a single
+    // rounded factor would bias every residual the same way
     __shared__ float2 s_ih[2];
     if (threadIdx.x == 0) {
         if (EPI == EPI_STAGE) s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
-        const double six_fl = 6.0 * (double)(float)(1.0 / 6.0);
-        s_ih[0] = f64_to_f32x2(-0.5 * a.inv_h[0] / six_fl);
-        s_ih[1] = f64_to_f32x2(-0.5 * a.inv_h[1] / six_fl);
+        s_ih[0] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[0]);
+        s_ih[1] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[1]);
     }
     const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
     const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
@@ -372,9 +373,11 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     // Face j's WENO(+) window takes the pairs a = j-3..j (indices j..j+3), its
     // mirrored WENO(-) window the pairs a = j+1..j-2 read backwards (indices
     // j+4..j+1).  Each run leaves a cell its pair's difference plus the change
-    // of the doubled correction across the cell (weno5d_cells2).
+    // of the correction across the cell (weno5d_cells2), both 6/4 of their
+    // values; on differences scaled by 1/4 the smoothness indicators carry
+    // 4 (1/4)^2 = 1/4 times beta, so Geps = eps / 4.
     {
-        const float Geps = (float)(4.0 / 9.0) * a.eps_f;
+        const float Geps = 0.25f * a.eps_f;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
         const int blk = sg * 2 + pr;
         const float2 *p;
@@ -403,8 +406,8 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     __syncthreads();
 
     // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y: the sum of the
-    // two runs' parts of the cell is 2 * 6 fl(1/6) times each flux difference,
-    // removed by the exact factor pairs s_ih
+    // two runs' parts of the cell is 3/2 times each flux difference, removed by
+    // the factor pairs s_ih
     float r[NF];
     {
         const float2 ihx = s_ih[0], ihy = s_ih[1];

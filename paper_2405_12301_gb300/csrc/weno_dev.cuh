@@ -274,12 +274,11 @@ __device__ __forceinline__ float weno5_pm(float2 a, float2 b, float2 c, float2 d
 // second differences and beta parts of the weno5 comment, the correction of a
 // window to its centre value c is
 //   sum_r omega_r v^(r) - c = (D2 + 2 D3)/6 + (w0 (t1 - t0) - 2 w2 (t1 - t2)) / (6 sum w).
-// p holds Dt = D / 3, so that the run returns twice the correction (the
-// doubled split fluxes of the callers):
-//   2 (sum_r omega_r v^(r) - c) = Ft + (w0 (tt1 - tt0) - 2 w2 (tt1 - tt2)) / sum w,
-//   Ft = Dt2 + 2 Dt3,  tt = t / 3,
-// and (13/3) tt_r^2 + st_r^2 = (4/9) beta_r (st = s / 3), so
-// G_r = (13/3) tt_r^2 + st_r^2 + Geps with Geps = (4/9) eps is (4/9)(beta_r + eps),
+// p holds Dt = s D for a scale s, and the run returns 6 s times the correction:
+//   6 s (sum_r omega_r v^(r) - c) = Ft + (w0 (tt1 - tt0) - 2 w2 (tt1 - tt2)) / sum w,
+//   Ft = Dt2 + 2 Dt3,  tt = s t,
+// with (13/3) tt_r^2 + st_r^2 = 4 s^2 beta_r (st = s s_r), so that
+// G_r = (13/3) tt_r^2 + st_r^2 + Geps with Geps = 4 s^2 eps is 4 s^2 (beta_r + eps),
 // and the weights w_r = d_r / G_r^2 up to a common factor are formed as
 // (3 g1 g2, 6 g0 g2, g0 g1) with g = G^2 (d = (3, 6, 1) / 10).  Window m takes
 // Dt1..Dt4 = p[m s] .. p[(m + 3) s] and writes to out[m os]; each window loads
@@ -326,8 +325,8 @@ __device__ __forceinline__ void weno5d_slide2(const float2 *p, int s, float Geps
 // output for window m, cell m - 1 (between the faces of windows m - 1 and m)
 // receives 6 D2_m + (C_m - C_{m-1}) (FWD; D2_m the window's second
 // difference, the cell's own pair), or -6 D2_m + (C_{m-1} - C_m) for a run read
-// backwards (!FWD), K - 1 values to out[(m - 1) os].  Those are the parts of a
-// cell's doubled flux difference that one run contributes (k_xy2 phase C).
+// backwards (!FWD), K - 1 values to out[(m - 1) os].  Those are 6 s times the
+// parts of a cell's flux difference that one run contributes (k_xy2 phase C).
 template <int K, bool FWD>
 __device__ __forceinline__ void weno5d_cells2(const float2 *p, int s, float Geps_, float2 *out, int os)
 {

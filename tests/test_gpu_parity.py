@@ -335,13 +335,18 @@ def test_bulk_l1_within_1p1_of_fp64_above_floor(W, N):
 
 @pytest.mark.parametrize("jumps", [False, True])
 def test_bulk_periodic_conservation_drift_is_bounded(W, jumps):
-    """FP32-bulk conserves up to the FP32 rounding of interface fluxes: an
-    interface on a tile boundary is formed by two CTAs relative to two line
-    references, so each such interface may differ by ~2^-24 V_tile (V_tile the
-    flux variation across a tile).  Per step that moves a sum by at most
-    (cells / S_min) * 2^-24 * V * dt / h, i.e. a relative drift per step of
-    2^-24 * (dt / h) * V / (S_min * mean |U_f|), S_min = 26 cells; the bound
-    below takes V = (1 + alpha) * (range of U_f + range of rho E) and 4x margin."""
+    """FP32-bulk (2D, pair-difference form): every interface's WENO correction
+    is formed from the same neighbour differences by both CTAs that touch it,
+    so the periodic sums move only by the FP32 rounding of the per-cell terms:
+    each neighbour difference D(a, b) enters one cell, with a rounding of a few
+    2^-24 times the size of its terms, ~(1 + alpha + |u|) |U_b - U_a|, and the
+    cell's FP32 increment rounds once more.  Summed with absolute values, per
+    stage a sum moves by at most K 2^-24 (dt / h) (1 + alpha + |u|) TV_f, TV_f the
+    sum over cells and directions of |U_f(i) - U_f(i - e_d)| + |E(i) - E(i - e_d)|
+    (K = 8 roundings).  The rounding errors are not correlated, so the drift is
+    far below that worst case: it is also held to 4e-9 relative after 50 steps,
+    about 4x the largest drift measured on this state; a per-tile reference
+    frame (interfaces on tile edges formed in two frames) drifted 1.4e-8."""
     n = (128, 96)
     cfg = O.Cfg(dim=2, n=n)
     U0 = I.random_state(2, n, seed=17, jumps=jumps)
@@ -353,13 +358,15 @@ def test_bulk_periodic_conservation_drift_is_bounded(W, jumps):
     s.run(Ud, 1e9, max_steps=steps)
     s1 = np.array(s.sums(Ud))
     alpha = O.alpha_max(cfg, U0)
+    umax = float((np.abs(U0[1:3]) / U0[0]).max())
     dt_h = 0.5 / alpha
     for f in range(4):
-        V = (1 + alpha) * (np.ptp(U0[f]) + np.ptp(U0[3]))
-        bound = 4 * steps * 2.0 ** -24 * dt_h * V / (26 * np.abs(U0[f]).mean())
+        tv = sum(np.abs(U0[g] - np.roll(U0[g], 1, axis=ax)).sum() for ax in (1, 2) for g in (f, 3))
+        bound = 3 * steps * 8 * 2.0 ** -24 * dt_h * (1 + alpha + umax) * tv / np.abs(U0[f]).sum()
         drift = abs(s1[f] - s0[f]) / np.abs(U0[f]).sum()
-        print("bulk drift f=%d: %.3e (bound %.3e)" % (f, drift, bound))
+        print("bulk drift f=%d: %.3e (worst-case bound %.3e)" % (f, drift, bound))
         assert drift <= bound
+        assert drift <= 4e-9
 
 
 # ----------------------------------------------------- full-size workloads
