@@ -59,14 +59,17 @@ constexpr int PXP = PX + 2;                   // their row pitch in float2 (odd:
 constexpr int PY = TY + 5;                    // y pairs per column: a = row -3..TY+1
 constexpr int NDX = PXP * TY;                 // one [sign][component pair] block of x differences
 constexpr int NDY = PY * TX;                  // one block of y differences
-constexpr int NC = TX * TY;                   // cells per block of run outputs
+constexpr int NC = TX * TY;                   // cells per block of y-run outputs
+constexpr int CXP = TX + 1;                   // row pitch of the x-run outputs (float2): the
+                                              // 8 rows of a warp's x runs then hit distinct banks
+constexpr int NCX = CXP * TY;                 // cells per block of x-run outputs
 // shared memory: differences, then the points (phases A-F) or the runs'
 // per-cell outputs (W-C)
 constexpr size_t DX_OFF = 0;
 constexpr size_t DY_OFF = DX_OFF + sizeof(float2) * 4 * NDX;
 constexpr size_t R_OFF = DY_OFF + sizeof(float2) * 4 * NDY;
 constexpr size_t PTS_BYTES = sizeof(float4) * 2 * NPT;
-constexpr size_t CELL_BYTES = sizeof(float2) * 8 * NC;
+constexpr size_t CELL_BYTES = sizeof(float2) * 4 * (NC + NCX);
 constexpr size_t BYTES = R_OFF + (PTS_BYTES > CELL_BYTES ? PTS_BYTES : CELL_BYTES);
 
 __device__ __forceinline__ int own_slot(int lx, int ly) { return ly * TX + lx; }
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     float2 *Dy = reinterpret_cast<float2 *>(smem + DY_OFF);   // [sign][pair][PY][TX]
     float4 *Ph = reinterpret_cast<float4 *>(smem + R_OFF);    // [NPT] hi parts (phases A-F)
     float4 *Pl = Ph + NPT;                                    // [NPT] lo parts
-    float2 *Px = reinterpret_cast<float2 *>(smem + R_OFF);    // [sign][pair][TY][TX] (phases W-C)
-    float2 *Py = Px + 4 * NC;                                 // [sign][pair][TY][TX]
+    float2 *Px = reinterpret_cast<float2 *>(smem + R_OFF);    // [sign][pair][TY][CXP] (phases W-C)
+    float2 *Py = Px + 4 * NCX;                                // [sign][pair][TY][TX]
 
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         } else {
             const int ly = lane & 7, j0 = (lane >> 3) * 8;
             p = Dx + blk * NDX + ly * PXP + j0;
-            out = Px + blk * NC + ly * TX + j0;
+            out = Px + blk * NCX + ly * CXP + j0;
             st = 1;
             os = 1;
         }
@@ -411,10 +414,10 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     float r[NF];
     {
         const float2 ihx = s_ih[0], ihy = s_ih[1];
-        const int c = ty * TX + tx;
+        const int c = ty * TX + tx, cx = ty * CXP + tx;
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
-            const float2 sx = add2(Px[pr * NC + c], Px[(2 + pr) * NC + c]);
+            const float2 sx = add2(Px[pr * NCX + cx], Px[(2 + pr) * NCX + cx]);
             const float2 sy = add2(Py[pr * NC + c], Py[(2 + pr) * NC + c]);
             const float2 rr = fma2(sy, bc2(ihy.x), fma2(sy, bc2(ihy.y), fma2(sx, bc2(ihx.x), mul2(sx, bc2(ihx.y)))));
             r[2 * pr] = rr.x;
