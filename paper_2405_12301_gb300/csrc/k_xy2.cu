@@ -22,6 +22,11 @@
 //   * the rounding of every WENO input scales with the difference of two
 //     neighbours, not with the variation across a tile.
 //
+// Stage state layout (this kernel): cell-interleaved, hl as float2 [cell][4]
+// (read as two float4: hi/lo of rho and m_x, then of m_y and E) and Delta as
+// float [cell][4] (one float4), so a point is three loads.  (The 3D kernels
+// keep the same stage state field by field, [f][cell].)
+//
 // Stage state (Eq. tt-ssprk3 without rounding, written on increments): with
 // U^(k) = U^n + Delta_k, Delta_1 = dt L(U^n), Delta_2 = (Delta_1 + dt L(U^1)) / 4,
 // Delta_3 = 2 (Delta_2 + dt L(U^2)) / 3 and U^{n+1} = U^n + Delta_3.  Stage 1
@@ -173,10 +178,11 @@ __device__ __noinline__ PointHL load_point_bc(const double *U, const float2 *hl,
     }
     const long long src = (long long)cy * nx + cx;
     if (from_hl) {
-        const float2 q0 = hl[src], q1 = hl[N + src], q2 = hl[2 * N + src], q3 = hl[3 * N + src];
-        const float d0 = din[src], d1 = din[N + src], d2 = din[2 * N + src], d3 = din[3 * N + src];
-        p.h = make_float4(q0.x, q1.x, q2.x, q3.x);
-        p.l = make_float4(q0.y + d0, q1.y + d1, q2.y + d2, q3.y + d3);
+        const float4 q01 = reinterpret_cast<const float4 *>(hl)[2 * src];
+        const float4 q23 = reinterpret_cast<const float4 *>(hl)[2 * src + 1];
+        const float4 d = reinterpret_cast<const float4 *>(din)[src];
+        p.h = make_float4(q01.x, q01.z, q23.x, q23.z);
+        p.l = make_float4(q01.y + d.x, q01.w + d.y, q23.y + d.z, q23.w + d.w);
     } else {
         split_f64(U[src], p.h.x, p.l.x);
         split_f64(U[N + src], p.h.y, p.l.y);
@@ -246,12 +252,11 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         }
         const long long src = (long long)(y0 + ly) * nx + (x0 + lx);
         if constexpr (from_hl) {
-            const float2 *hl = a.hl + src;
-            const float *d = a.din + src;
-            const float2 q0 = __ldg(hl), q1 = __ldg(hl + N), q2 = __ldg(hl + 2 * N), q3 = __ldg(hl + 3 * N);
-            const float d0 = __ldg(d), d1 = __ldg(d + N), d2 = __ldg(d + 2 * N), d3 = __ldg(d + 3 * N);
-            h = make_float4(q0.x, q1.x, q2.x, q3.x);
-            l = make_float4(q0.y + d0, q1.y + d1, q2.y + d2, q3.y + d3);
+            const float4 *hl = reinterpret_cast<const float4 *>(a.hl) + 2 * src;
+            const float4 q01 = __ldg(hl), q23 = __ldg(hl + 1);
+            const float4 d = __ldg(reinterpret_cast<const float4 *>(a.din) + src);
+            h = make_float4(q01.x, q01.z, q23.x, q23.z);
+            l = make_float4(q01.y + d.x, q01.w + d.y, q23.y + d.z, q23.w + d.w);
         } else {
             const double *u = a.U + src;
             split_f64(__ldg(u), h.x, l.x);
@@ -291,10 +296,9 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         load_point(tx, ty, h, l);
         if (halo) load_point(hx, hy, h2, l2);
         if (EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
-            a.hl[cell] = make_float2(h.x, l.x);
-            a.hl[N + cell] = make_float2(h.y, l.y);
-            a.hl[2 * N + cell] = make_float2(h.z, l.z);
-            a.hl[3 * N + cell] = make_float2(h.w, l.w);
+            float4 *hw = reinterpret_cast<float4 *>(a.hl) + 2 * cell;
+            hw[0] = make_float4(h.x, l.x, h.y, l.y);
+            hw[1] = make_float4(h.z, l.z, h.w, l.w);
         }
         Ph[own_slot(tx, ty)] = h;
         Pl[own_slot(tx, ty)] = l;
@@ -360,10 +364,19 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     // latency: Delta_k (stages 2, 3) and the hi part of U^n (its wavespeed)
     float dk[NF] = {0.0f, 0.0f, 0.0f, 0.0f}, hn[NF] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (EPI == EPI_STAGE && own) {
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            hn[f] = a.hl[f * N + cell].x;  // stage 1 wrote it in phase A (a plain, coherent load)
-            if (ST > 0) dk[f] = __ldg(a.din + f * N + cell);
+        // stage 1 wrote hl in phase A (plain, coherent loads)
+        const float4 q01 = reinterpret_cast<const float4 *>(a.hl)[2 * cell];
+        const float4 q23 = reinterpret_cast<const float4 *>(a.hl)[2 * cell + 1];
+        hn[0] = q01.x;
+        hn[1] = q01.z;
+        hn[2] = q23.x;
+        hn[3] = q23.z;
+        if (ST > 0) {
+            const float4 d = __ldg(reinterpret_cast<const float4 *>(a.din) + cell);
+            dk[0] = d.x;
+            dk[1] = d.y;
+            dk[2] = d.z;
+            dk[3] = d.w;
         }
     }
 
@@ -440,16 +453,16 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const float2 bdt = s_bdt;
         constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
         constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
-        float q[NF];
+        float q[NF], dn[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             float t = bdt.y * r[f];
             if (ST > 0) t = fmaf(c_hi, dk[f], fmaf(c_lo, dk[f], t));
-            const float d = fmaf(bdt.x, r[f], t);
-            if (ST < 2) a.dout[f * N + cell] = d;
-            else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
-            q[f] = hn[f] + d;  // the new state in FP32, for the wavespeed
+            dn[f] = fmaf(bdt.x, r[f], t);
+            if (ST == 2) a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(dn[f]);
+            q[f] = hn[f] + dn[f];  // the new state in FP32, for the wavespeed
         }
+        if (ST < 2) reinterpret_cast<float4 *>(a.dout)[cell] = make_float4(dn[0], dn[1], dn[2], dn[3]);
         s = wavespeed_f32<2>(q, a.gamma_f, bad);
         if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);
     }
