@@ -501,6 +501,39 @@ def test_inflow_fp64_matches_oracle(W, dim, n, bc):
     assert (np.abs(host(Rd) - Rref) <= _variation_tol(cfg, U, Rref, aref[0], used)).all()
 
 
+@pytest.mark.parametrize("dim,n,bc,inflow", [c + (False,) for c in CASES] + [c + (True,) for c in INFLOW_CASES])
+def test_run_bulk_tracks_oracle_run(W, dim, n, bc, inflow):
+    """FP32-bulk runs through all three stages (stages 2 and 3 read the stored
+    split of U^n plus the FP32 increments), with every boundary rule, against
+    the oracle's FP64 run to t = 0.03: the same number of steps, and every cell
+    within 2 T tol_f, tol_f the FP32-bulk residual bound of the initial state
+    (an error of at most tol_f in each stage's residual moves the state by at
+    most dt tol_f per step; the factor 2 covers its propagation)."""
+    nf = dim + 2
+    st = None
+    if inflow:
+        st = [[_qin(dim, 1.4, 0.9, 1.2), _qin(dim, 0.8, -0.3, 0.7)],
+              [_qin(dim, 1.1, 0.2, 1.0), _qin(dim, 0.9, -0.5, 0.8)],
+              [_qin(dim, 1.2, 0.4, 0.9), _qin(dim, 1.0, -0.2, 1.1)]]
+        st = [[side[:nf] + [0.0] * (5 - nf) for side in d] for d in st]
+    cfg = O.Cfg(dim=dim, n=n, bc=bc, bc_state=st)
+    U = I.random_state(dim, n, seed=600 + sum(n), jumps=True)
+    T_end = 0.03
+    Uref, steps, _ = O.run(cfg, U, T_end, cfl=0.5)
+    Rref, aref = O.residual(cfg, U)
+    used = [st[k][side][:nf] for k in range(dim) for side in range(2) if bc[k][side] == IN] if inflow else ()
+    tol = _variation_tol(cfg, U, Rref, aref[0], used)
+    s = solver(W, cfg, precision=1)
+    Ud = dev(U)
+    s.set_time(0.0)
+    assert s.run(Ud, T_end, graph_steps=4) == steps
+    Ug = host(Ud)
+    for f in range(nf):
+        bound = 2 * T_end * tol[f].max()
+        err = float(np.abs(Ug[f] - Uref[f]).max())
+        assert err <= bound, (f, err, bound)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_full_size_384_cube_z_only_field_matches_1d_oracle(W, precision):
     """384^3 (the larger 3D grid, a 2.26 GB state): a state varying along z only
