@@ -55,9 +55,9 @@ namespace xy2 {
 constexpr int NT = 256;
 constexpr int TX = 32, TY = 8;
 constexpr int NOWN = TX * TY;                 // 256 own points
-constexpr int XH0 = NOWN;                     // x-halo slots: [row][6] (cols -3..-1, TX..TX+2)
-constexpr int YH0 = XH0 + 6 * TY;             // y-halo slots: [6][col] (rows -3..-1, TY..TY+2)
-constexpr int NPT = YH0 + 6 * TX;             // 496 points
+constexpr int YH0 = NOWN;                     // y-halo slots: [6][col] (rows -3..-1, TY..TY+2)
+constexpr int XH0 = YH0 + 6 * TX;             // x-halo slots: [6][row] (cols -3..-1, TX..TX+2)
+constexpr int NPT = XH0 + 6 * TY;             // 496 points; halo point k (thread k) in slot YH0 + k
 constexpr int NHY = 6 * TX, NHALO = NHY + 6 * TY;  // 192 y-halo + 48 x-halo points
 constexpr int PX = TX + 5;                    // x pairs per row: a = col -3..TX+1
 constexpr int PXP = PX + 2;                   // their row pitch in float2 (odd: conflict-free runs)
@@ -77,8 +77,9 @@ constexpr size_t PTS_BYTES = sizeof(float4) * 2 * NPT;
 constexpr size_t CELL_BYTES = sizeof(float2) * 4 * (NC + NCX);
 constexpr size_t BYTES = R_OFF + (PTS_BYTES > CELL_BYTES ? PTS_BYTES : CELL_BYTES);
 
+static_assert(TX == 32 && TY == 8, "the halo decode takes lane bits for TX and TY");
 __device__ __forceinline__ int own_slot(int lx, int ly) { return ly * TX + lx; }
-__device__ __forceinline__ int xh_slot(int lx, int ly) { return XH0 + ly * 6 + (lx < 0 ? lx + 3 : lx - TX + 3); }
+__device__ __forceinline__ int xh_slot(int lx, int ly) { return XH0 + (lx < 0 ? lx + 3 : lx - TX + 3) * TY + ly; }
 __device__ __forceinline__ int yh_slot(int lx, int ly) { return YH0 + (ly < 0 ? ly + 3 : ly - TY + 3) * TX + lx; }
 }  // namespace xy2
 
@@ -217,14 +218,19 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     // themselves, and the runs return 6/4 of the corrections), and a single
     // rounded factor would bias every residual the same way
     __shared__ float2 s_ih[2];
+    __shared__ float2 s_al;  // the LF alpha of x and y in FP32 (converted once per block)
+    __shared__ unsigned s_max[3];  // the block's wavespeed maxima (FP32 bit patterns)
+    __shared__ int s_bad;
     if (threadIdx.x == 0) {
+        s_max[0] = s_max[1] = s_max[2] = 0u;
+        s_bad = 0;
         if (EPI == EPI_STAGE) s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
         s_ih[0] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[0]);
         s_ih[1] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[1]);
+        const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+        s_al = make_float2(f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha),
+                           f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha));
     }
-    const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
-    const float alX = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha);
-    const float alY = f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha);
 
     const int nx = a.n[0], ny = a.n[1];
     const long long N = a.N;
@@ -272,22 +278,21 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     int hk = 0, hslot = 0, bslot = 0, hx = 0, hy = 0;
     bool hdirx = false;
     if (halo) {
-        int t = threadIdx.x;
+        const int t = threadIdx.x;
+        hslot = YH0 + t;
         if (t < NHY) {     // y halo: rows -3..-1 and TY..TY+2 of every tile column
             hx = t & 31;
             hk = t >> 5;
             hy = hk < 3 ? hk - 3 : TY + hk - 3;
-            hslot = YH0 + hk * TX + hx;
             // its upper pair, except from the last row; row -1's upper point is own row 0
-            bslot = hk == 2 ? own_slot(hx, 0) : YH0 + (hk + 1) * TX + hx;
+            bslot = hk == 2 ? own_slot(hx, 0) : hslot + TX;
         } else {           // x halo: columns -3..-1 and TX..TX+2 of every tile row
-            t -= NHY;
-            hy = t / 6;
-            hk = t - hy * 6;
+            const int u = t - NHY;
+            hk = u >> 3;
+            hy = u & 7;
             hx = hk < 3 ? hk - 3 : TX + hk - 3;
             hdirx = true;
-            hslot = XH0 + hy * 6 + hk;
-            bslot = hk == 2 ? own_slot(0, hy) : XH0 + hy * 6 + hk + 1;
+            bslot = hk == 2 ? own_slot(0, hy) : hslot + TY;
         }
     }
     const bool hpair = halo && hk != 5;
@@ -311,6 +316,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     // ---- phase F: neighbour-pair differences
     const float gm1 = a.gm1_f;
+    const float alX = s_al.x, alY = s_al.y;
     {
         const int sa = own_slot(tx, ty);
         const int sbx = tx + 1 < TX ? own_slot(tx + 1, ty) : xh_slot(TX, ty);
@@ -341,13 +347,11 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         float2 *Dd;
         int nd;
         if (hdirx) {
-            const int hy = (threadIdx.x - NHY) / 6;
             pair_diff1<0>(ha, la, A, hb, lb, alX, gm1, dp, dm);
             o = hy * PXP + (hk < 3 ? hk : TX + hk);  // a col + 3
             Dd = Dx;
             nd = NDX;
         } else {
-            const int hx = threadIdx.x & 31;
             pair_diff1<1>(ha, la, A, hb, lb, alY, gm1, dp, dm);
             o = (hk < 3 ? hk : TY + hk) * TX + hx;  // (a row + 3) * TX + col
             Dd = Dy;
@@ -466,11 +470,9 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         s = wavespeed_f32<2>(q, a.gamma_f, bad);
         if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);
     }
-    block_max_publish_f32(s, bad, &a.ctl->alpha[a.slot_out], &a.ctl->status);
-    if constexpr (PD) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) block_max_publish_f32(sd[e], false, &a.ctl->alpha_dir[a.slot_out][e], &a.ctl->status);
-    }
+    const float v[3] = {s, sd[0], sd[1]};
+    block_max_publish_f32_1b<PD ? 3 : 1>(v, bad, s_max, &s_bad, &a.ctl->alpha[a.slot_out],
+                                         &a.ctl->alpha_dir[a.slot_out][0], &a.ctl->status);
 }
 
 template <int EPI, bool PD, int ST>

@@ -601,6 +601,31 @@ __device__ __forceinline__ void block_max_publish_f32(float v, bool bad, unsigne
     }
 }
 
+// The same with one barrier: K values, each reduced per warp with the
+// single-instruction reduction and combined with a shared-memory atomicMax
+// into s_max[K] (with the non-physical flag into *s_bad); the caller zeroes
+// s_max and *s_bad before a barrier that precedes this call.  Value 0 goes to
+// *slot0, value k > 0 to slot_dir[k - 1].  Every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ void block_max_publish_f32_1b(const float *v, bool bad, unsigned *s_max, int *s_bad,
+                                                         unsigned long long *slot0, unsigned long long *slot_dir,
+                                                         int *status)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(v[k]));
+        if ((threadIdx.x & 31) == 0 && m > 0u) atomicMax(s_max + k, m);
+    }
+    if (bad) *s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const unsigned mm = s_max[threadIdx.x];
+        unsigned long long *sl = threadIdx.x == 0 ? slot0 : slot_dir + (threadIdx.x - 1);
+        if (mm > 0u) atomicMax(sl, (unsigned long long)__double_as_longlong(f32_to_f64(__uint_as_float(mm))));
+    }
+    if (threadIdx.x == 0 && *s_bad) atomicOr(status, ST_NONPHYSICAL);
+}
+
 // Block-wide max of a non-negative value, then one atomicMax per block on the
 // 64-bit pattern of the double.  Also ORs the block's non-physical flag into
 // the status word.  Every thread of the block must call it.
