@@ -22,10 +22,11 @@
 //   * the rounding of every WENO input scales with the difference of two
 //     neighbours, not with the variation across a tile.
 //
-// Stage state layout (this kernel): cell-interleaved, hl as float2 [cell][4]
-// (read as two float4: hi/lo of rho and m_x, then of m_y and E) and Delta as
-// float [cell][4] (one float4), so a point is three loads.  (The 3D kernels
-// keep the same stage state field by field, [f][cell].)
+// Stage state layout (this kernel): the hi parts of a cell's four fields as one
+// float4 in plane H = hl[0 .. N), their lo parts in plane L = hl[N .. 2N), and
+// Delta as float [cell][4] (one float4), so a point is three loads and its lo
+// part plus Delta two packed adds.  (The 3D kernels keep the same stage state
+// field by field, [f][cell].)
 //
 // Stage state (Eq. tt-ssprk3 without rounding, written on increments): with
 // U^(k) = U^n + Delta_k, Delta_1 = dt L(U^n), Delta_2 = (Delta_1 + dt L(U^1)) / 4,
@@ -91,13 +92,18 @@ struct Prim2 {
     float rho, u, v, H, mx, my;
 };
 
+__device__ __forceinline__ float2 lo2(const float4 q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 hi2(const float4 q) { return make_float2(q.z, q.w); }
+__device__ __forceinline__ float4 cat4(const float2 a, const float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
 __device__ __forceinline__ Prim2 prim2(const float4 h, const float4 l, float gm1)
 {
     Prim2 P;
-    P.rho = __fadd_rn(h.x, l.x);
-    P.mx = __fadd_rn(h.y, l.y);
-    P.my = __fadd_rn(h.z, l.z);
-    const float E = __fadd_rn(h.w, l.w);
+    const float2 q01 = add2(lo2(h), lo2(l)), q23 = add2(hi2(h), hi2(l));
+    P.rho = q01.x;
+    P.mx = q01.y;
+    P.my = q23.x;
+    const float E = q23.y;
     const float ir = fast_rcp(P.rho);
     P.u = __fmul_rn(P.mx, ir);
     P.v = __fmul_rn(P.my, ir);
@@ -158,7 +164,7 @@ struct PointHL {
     float4 h, l;
 };
 
-__device__ __noinline__ PointHL load_point_bc(const double *U, const float2 *hl, const float *din, long long N,
+__device__ __noinline__ PointHL load_point_bc(const double *U, const float4 *hl, const float *din, long long N,
                                               int nx, int ny, int bx0, int bx1, int by0, int by1,
                                               const double *bcs, bool from_hl, int cx, int cy)
 {
@@ -179,11 +185,9 @@ __device__ __noinline__ PointHL load_point_bc(const double *U, const float2 *hl,
     }
     const long long src = (long long)cy * nx + cx;
     if (from_hl) {
-        const float4 q01 = reinterpret_cast<const float4 *>(hl)[2 * src];
-        const float4 q23 = reinterpret_cast<const float4 *>(hl)[2 * src + 1];
-        const float4 d = reinterpret_cast<const float4 *>(din)[src];
-        p.h = make_float4(q01.x, q01.z, q23.x, q23.z);
-        p.l = make_float4(q01.y + d.x, q01.w + d.y, q23.y + d.z, q23.w + d.w);
+        const float4 l = hl[N + src], d = reinterpret_cast<const float4 *>(din)[src];
+        p.h = hl[src];
+        p.l = cat4(add2(lo2(l), lo2(d)), add2(hi2(l), hi2(d)));
     } else {
         split_f64(U[src], p.h.x, p.l.x);
         split_f64(U[N + src], p.h.y, p.l.y);
@@ -246,11 +250,12 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + cell));
     }
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
+    float4 *Hl = reinterpret_cast<float4 *>(a.hl);  // planes H and L of the stage state
 
     // ---- phase A: a point's FP32 hi/lo state, boundary rule on ghost indices
     auto load_point = [&](int lx, int ly, float4 &h, float4 &l) {
         if (!interior) {
-            const PointHL p = load_point_bc(a.U, a.hl, a.din, N, nx, ny, a.bc[0][0], a.bc[0][1], a.bc[1][0],
+            const PointHL p = load_point_bc(a.U, Hl, a.din, N, nx, ny, a.bc[0][0], a.bc[0][1], a.bc[1][0],
                                             a.bc[1][1], a.bcs, from_hl, x0 + lx, y0 + ly);
             h = p.h;
             l = p.l;
@@ -258,11 +263,9 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         }
         const long long src = (long long)(y0 + ly) * nx + (x0 + lx);
         if constexpr (from_hl) {
-            const float4 *hl = reinterpret_cast<const float4 *>(a.hl) + 2 * src;
-            const float4 q01 = __ldg(hl), q23 = __ldg(hl + 1);
-            const float4 d = __ldg(reinterpret_cast<const float4 *>(a.din) + src);
-            h = make_float4(q01.x, q01.z, q23.x, q23.z);
-            l = make_float4(q01.y + d.x, q01.w + d.y, q23.y + d.z, q23.w + d.w);
+            const float4 lo = __ldg(Hl + N + src), d = __ldg(reinterpret_cast<const float4 *>(a.din) + src);
+            h = __ldg(Hl + src);
+            l = cat4(add2(lo2(lo), lo2(d)), add2(hi2(lo), hi2(d)));
         } else {
             const double *u = a.U + src;
             split_f64(__ldg(u), h.x, l.x);
@@ -301,9 +304,8 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         load_point(tx, ty, h, l);
         if (halo) load_point(hx, hy, h2, l2);
         if (EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
-            float4 *hw = reinterpret_cast<float4 *>(a.hl) + 2 * cell;
-            hw[0] = make_float4(h.x, l.x, h.y, l.y);
-            hw[1] = make_float4(h.z, l.z, h.w, l.w);
+            Hl[cell] = h;
+            Hl[N + cell] = l;
         }
         Ph[own_slot(tx, ty)] = h;
         Pl[own_slot(tx, ty)] = l;
@@ -366,22 +368,10 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     // the epilogue's own-cell inputs, loaded now so that phase W hides their
     // latency: Delta_k (stages 2, 3) and the hi part of U^n (its wavespeed)
-    float dk[NF] = {0.0f, 0.0f, 0.0f, 0.0f}, hn[NF] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float4 dk = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hn = dk;
     if (EPI == EPI_STAGE && own) {
-        // stage 1 wrote hl in phase A (plain, coherent loads)
-        const float4 q01 = reinterpret_cast<const float4 *>(a.hl)[2 * cell];
-        const float4 q23 = reinterpret_cast<const float4 *>(a.hl)[2 * cell + 1];
-        hn[0] = q01.x;
-        hn[1] = q01.z;
-        hn[2] = q23.x;
-        hn[3] = q23.z;
-        if (ST > 0) {
-            const float4 d = __ldg(reinterpret_cast<const float4 *>(a.din) + cell);
-            dk[0] = d.x;
-            dk[1] = d.y;
-            dk[2] = d.z;
-            dk[3] = d.w;
-        }
+        hn = Hl[cell];  // stage 1 wrote it in phase A (a plain, coherent load)
+        if (ST > 0) dk = __ldg(reinterpret_cast<const float4 *>(a.din) + cell);
     }
 
     // ---- phase W: WENO corrections of every face (the points are dead now;
@@ -428,7 +418,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     // ---- phase C: -(F^_{i+1} - F^_i)/h_x - (G^_{j+1} - G^_j)/h_y: the sum of the
     // two runs' parts of the cell is 3/2 times each flux difference, removed by
     // the factor pairs s_ih
-    float r[NF];
+    float2 r[2];  // the residual, fields (rho, m_x) and (m_y, E)
     {
         const float2 ihx = s_ih[0], ihy = s_ih[1];
         const int c = ty * TX + tx, cx = ty * CXP + tx;
@@ -436,15 +426,15 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         for (int pr = 0; pr < 2; ++pr) {
             const float2 sx = add2(Px[pr * NCX + cx], Px[(2 + pr) * NCX + cx]);
             const float2 sy = add2(Py[pr * NC + c], Py[(2 + pr) * NC + c]);
-            const float2 rr = fma2(sy, bc2(ihy.x), fma2(sy, bc2(ihy.y), fma2(sx, bc2(ihx.x), mul2(sx, bc2(ihx.y)))));
-            r[2 * pr] = rr.x;
-            r[2 * pr + 1] = rr.y;
+            r[pr] = fma2(sy, bc2(ihy.x), fma2(sy, bc2(ihy.y), fma2(sx, bc2(ihx.x), mul2(sx, bc2(ihx.y)))));
         }
     }
     if (EPI == EPI_RHS) {
         if (own) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) a.Rout[f * N + cell] = f32_to_f64(r[f]);
+            a.Rout[cell] = f32_to_f64(r[0].x);
+            a.Rout[N + cell] = f32_to_f64(r[0].y);
+            a.Rout[2 * N + cell] = f32_to_f64(r[1].x);
+            a.Rout[3 * N + cell] = f32_to_f64(r[1].y);
         }
         return;
     }
@@ -457,16 +447,22 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const float2 bdt = s_bdt;
         constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
         constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
-        float q[NF], dn[NF];
+        float2 dn[2], qq[2];
+        const float2 dkp[2] = {lo2(dk), hi2(dk)}, hnp[2] = {lo2(hn), hi2(hn)};
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            float t = bdt.y * r[f];
-            if (ST > 0) t = fmaf(c_hi, dk[f], fmaf(c_lo, dk[f], t));
-            dn[f] = fmaf(bdt.x, r[f], t);
-            if (ST == 2) a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(dn[f]);
-            q[f] = hn[f] + dn[f];  // the new state in FP32, for the wavespeed
+        for (int pr = 0; pr < 2; ++pr) {  // field pairs, each lane rounded as the scalar form
+            float2 t = mul2(bc2(bdt.y), r[pr]);
+            if (ST > 0) t = fma2(bc2(c_hi), dkp[pr], fma2(bc2(c_lo), dkp[pr], t));
+            dn[pr] = fma2(bc2(bdt.x), r[pr], t);
+            qq[pr] = add2(hnp[pr], dn[pr]);  // the new state in FP32, for the wavespeed
         }
-        if (ST < 2) reinterpret_cast<float4 *>(a.dout)[cell] = make_float4(dn[0], dn[1], dn[2], dn[3]);
+        if (ST == 2) {
+            const float d4[NF] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
+#pragma unroll
+            for (int f = 0; f < NF; ++f) a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d4[f]);
+        }
+        const float q[NF] = {qq[0].x, qq[0].y, qq[1].x, qq[1].y};
+        if (ST < 2) reinterpret_cast<float4 *>(a.dout)[cell] = cat4(dn[0], dn[1]);
         s = wavespeed_f32<2>(q, a.gamma_f, bad);
         if (PD && !bad) dirspeeds_f32<2>(q, a.gamma_f, sd);
     }

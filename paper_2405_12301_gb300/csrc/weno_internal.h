@@ -20,7 +20,7 @@ struct SweepArgs {
     double *Rout;        // output of EPI_RHS
     // 2D FP32-bulk stage state (k_xy2): the FP32 hi/lo split of U^n, written
     // by stage 1, and the FP32 increments Delta_k = U^(k) - U^n
-    float2 *hl;          // [nf][N]
+    float2 *hl;          // 2D: planes H, L of float4 [N] each; 3D: [nf][N]
     const float *din;    // Delta_k read by stages 2 and 3
     float *dout;         // Delta_{k+1} written by stages 1 and 2
     Ctl *ctl;
