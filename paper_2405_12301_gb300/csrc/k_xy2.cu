@@ -390,27 +390,20 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         const float Geps = 0.25f * a.eps_f;
         const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, pr = w & 1, sg = (w >> 1) & 1;
         const int blk = sg * 2 + pr;
-        const float2 *p;
-        float2 *out;
-        int st, os;
+        // the strides are compile-time constants in each of the four calls, so
+        // every load and store of a run takes an immediate offset
         if (w < 4) {
-            p = Dy + blk * NDY + lane;
-            out = Py + blk * NC + lane;
-            st = TX;
-            os = TX;
+            const float2 *p = Dy + blk * NDY + lane;
+            float2 *out = Py + blk * NC + lane;
+            if (sg) weno5d_cells2<TY + 1, false>(p + 12 * TX, -TX, Geps, out + (TY - 1) * TX, -TX);
+            else weno5d_cells2<TY + 1, true>(p, TX, Geps, out, TX);
         } else {
             const int ly = lane & 7, j0 = (lane >> 3) * 8;
-            p = Dx + blk * NDX + ly * PXP + j0;
-            out = Px + blk * NCX + ly * CXP + j0;
-            st = 1;
-            os = 1;
-        }
-        if (sg) {  // WENO(-): differences j0+12 .. j0+1, cells j0+7 .. j0
-            p += 12 * st;
-            out += (TY - 1) * os;
-            weno5d_cells2<TY + 1, false>(p, -st, Geps, out, -os);
-        } else {
-            weno5d_cells2<TY + 1, true>(p, st, Geps, out, os);
+            const float2 *p = Dx + blk * NDX + ly * PXP + j0;
+            float2 *out = Px + blk * NCX + ly * CXP + j0;
+            // WENO(-): differences j0+12 .. j0+1, cells j0+7 .. j0
+            if (sg) weno5d_cells2<TY + 1, false>(p + 12, -1, Geps, out + (TY - 1), -1);
+            else weno5d_cells2<TY + 1, true>(p, 1, Geps, out, 1);
         }
     }
     __syncthreads();
