@@ -242,15 +242,18 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool own = gx < nx && gy < ny;
-    const long long cell = (long long)(gy < ny ? gy : ny - 1) * nx + (gx < nx ? gx : nx - 1);
+    // 32-bit cell indices (the host keeps N below 2^32) on 64-bit plane pointers
+    const unsigned cell = (unsigned)(gy < ny ? gy : ny - 1) * (unsigned)nx + (unsigned)(gx < nx ? gx : nx - 1);
     // stage 1 reads U^n as FP64; stages 2 and 3 read the stored split and Delta_{k-1}
     constexpr bool from_hl = EPI == EPI_STAGE && ST > 0;
     if (EPI == EPI_STAGE && ST == 2) {  // U^n at the own cell, for U^{n+1} = U^n + Delta_3
 #pragma unroll
-        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.U + f * N + cell));
+        for (int f = 0; f < NF; ++f) asm volatile("prefetch.global.L2 [%0];" ::"l"((a.U + f * N) + cell));
     }
     const bool interior = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= nx && y0 + TY + 3 <= ny;
     float4 *Hl = reinterpret_cast<float4 *>(a.hl);  // planes H and L of the stage state
+    float4 *Ll = Hl + N;
+    const float4 *Din = reinterpret_cast<const float4 *>(a.din);
 
     // ---- phase A: a point's FP32 hi/lo state, boundary rule on ghost indices
     auto load_point = [&](int lx, int ly, float4 &h, float4 &l) {
@@ -261,17 +264,17 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
             l = p.l;
             return;
         }
-        const long long src = (long long)(y0 + ly) * nx + (x0 + lx);
+        const unsigned src = (unsigned)(y0 + ly) * (unsigned)nx + (unsigned)(x0 + lx);
         if constexpr (from_hl) {
-            const float4 lo = __ldg(Hl + N + src), d = __ldg(reinterpret_cast<const float4 *>(a.din) + src);
+            const float4 lo = __ldg(Ll + src), d = __ldg(Din + src);
             h = __ldg(Hl + src);
             l = cat4(add2(lo2(lo), lo2(d)), add2(hi2(lo), hi2(d)));
         } else {
-            const double *u = a.U + src;
-            split_f64(__ldg(u), h.x, l.x);
-            split_f64(__ldg(u + N), h.y, l.y);
-            split_f64(__ldg(u + 2 * N), h.z, l.z);
-            split_f64(__ldg(u + 3 * N), h.w, l.w);
+            const double *u = a.U;
+            split_f64(__ldg(u + src), h.x, l.x);
+            split_f64(__ldg((u += N) + src), h.y, l.y);
+            split_f64(__ldg((u += N) + src), h.z, l.z);
+            split_f64(__ldg((u += N) + src), h.w, l.w);
         }
     };
 
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         if (halo) load_point(hx, hy, h2, l2);
         if (EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
             Hl[cell] = h;
-            Hl[N + cell] = l;
+            Ll[cell] = l;
         }
         Ph[own_slot(tx, ty)] = h;
         Pl[own_slot(tx, ty)] = l;
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     float4 dk = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hn = dk;
     if (EPI == EPI_STAGE && own) {
         hn = Hl[cell];  // stage 1 wrote it in phase A (a plain, coherent load)
-        if (ST > 0) dk = __ldg(reinterpret_cast<const float4 *>(a.din) + cell);
+        if (ST > 0) dk = __ldg(Din + cell);
     }
 
     // ---- phase W: WENO corrections of every face (the points are dead now;
@@ -424,10 +427,11 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     }
     if (EPI == EPI_RHS) {
         if (own) {
-            a.Rout[cell] = f32_to_f64(r[0].x);
-            a.Rout[N + cell] = f32_to_f64(r[0].y);
-            a.Rout[2 * N + cell] = f32_to_f64(r[1].x);
-            a.Rout[3 * N + cell] = f32_to_f64(r[1].y);
+            double *R = a.Rout;
+            R[cell] = f32_to_f64(r[0].x);
+            (R += N)[cell] = f32_to_f64(r[0].y);
+            (R += N)[cell] = f32_to_f64(r[1].x);
+            (R += N)[cell] = f32_to_f64(r[1].y);
         }
         return;
     }
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
         if (ST == 2) {
             const float d4[NF] = {dn[0].x, dn[0].y, dn[1].x, dn[1].y};
 #pragma unroll
-            for (int f = 0; f < NF; ++f) a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d4[f]);
+            for (int f = 0; f < NF; ++f) (a.Uout + f * N)[cell] = __ldg((a.U + f * N) + cell) + f32_to_f64(d4[f]);
         }
         const float q[NF] = {qq[0].x, qq[0].y, qq[1].x, qq[1].y};
         if (ST < 2) reinterpret_cast<float4 *>(a.dout)[cell] = cat4(dn[0], dn[1]);
@@ -489,6 +493,7 @@ static cudaError_t launch_xy2_s(const SweepArgs &a, cudaStream_t s)
 
 cudaError_t launch_xy2(int epi, const SweepArgs &a, cudaStream_t s)
 {
+    if (a.N >= (1ll << 32)) return cudaErrorInvalidValue;  // the kernel indexes cells in 32 bits
     if (epi == EPI_RHS) return a.per_dir ? launch_xy2_s<EPI_RHS, true>(a, s) : launch_xy2_s<EPI_RHS, false>(a, s);
     if (epi == EPI_STAGE) return a.per_dir ? launch_xy2_s<EPI_STAGE, true>(a, s) : launch_xy2_s<EPI_STAGE, false>(a, s);
     return cudaErrorInvalidValue;
