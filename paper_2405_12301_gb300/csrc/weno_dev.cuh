@@ -561,11 +561,21 @@ __device__ __forceinline__ void dirspeeds_f32(const float *q, float gamma, float
     for (int e = 0; e < D; ++e) sd[e] = fabsf(q[1 + e] * ir) + a;
 }
 
+// The FP32 wavespeed ||u|| + a feeds only the maximum behind alpha and dt,
+// where a relative error of a few ulp is immaterial, so it takes the
+// approximate reciprocal and square roots (one MUFU instruction each).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int D>
 __device__ __forceinline__ float wavespeed_f32(const float *q, float gamma, bool &bad)
 {
     const float rho = q[0];
-    const float ir = 1.0f / rho;
+    const float ir = fast_rcp(rho);
     float u2 = 0.0f;
 #pragma unroll
     for (int e = 0; e < D; ++e) {
@@ -574,7 +584,7 @@ __device__ __forceinline__ float wavespeed_f32(const float *q, float gamma, bool
     }
     const float p = (gamma - 1.0f) * (q[D + 1] - 0.5f * rho * u2);
     bad = !(rho > 0.0f) || !(p > 0.0f) || !isfinite(u2) || !isfinite(q[D + 1]);
-    return bad ? 0.0f : sqrtf(u2) + sqrtf(gamma * p * ir);
+    return bad ? 0.0f : sqrt_approx(u2) + sqrt_approx(gamma * p * ir);
 }
 
 // FP32 variant for the FP32-bulk kernels: the max runs on the bit patterns of
