@@ -181,19 +181,25 @@ __global__ void __launch_bounds__(xy::NT, BULK ? 5 : 1) k_xy(const SweepArgs a)
         else load_point(hx, hy, qd);
     }
 
-    // ---- reference state of the tile (FP32-bulk): its first cell
+    // ---- reference state of the tile (FP32-bulk): its first cell; the LF
+    // constants in FP32, converted once per block
+    __shared__ float2 s_al;
     if (BULK) {
         if (threadIdx.x < 32) {  // the tile's first cell is inside the grid
             float h0[NF], l0[NF];
             load_point_b(0, 0, h0, l0);
             RefState<D> r;
             make_ref_hl<D>(h0, l0, a.gm1_f, r);
-            if (threadIdx.x == 0) ref = r;
+            if (threadIdx.x == 0) {
+                ref = r;
+                const float ax = f64_to_f32(alx);
+                s_al = make_float2(ax, PD ? f64_to_f32(aly) : ax);
+            }
         }
         __syncthreads();
     }
-    const T alX = BULK ? (T)f64_to_f32(alx) : (T)alx;
-    const T alY = !PD ? alX : (BULK ? (T)f64_to_f32(aly) : (T)aly);
+    const T alX = BULK ? (T)s_al.x : (T)alx;
+    const T alY = BULK ? (T)s_al.y : (T)aly;
     const double gm1 = a.gamma - 1.0;
 
     // split fluxes of a point in one direction, stored at its slot of fx / fy

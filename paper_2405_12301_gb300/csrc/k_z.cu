@@ -31,8 +31,23 @@ template <bool BULK> struct Layout {
     static constexpr size_t F_off = 0;
     static constexpr size_t fz_off = (sizeof(T) * NF * NZI + 15) & ~size_t(15);
     static constexpr size_t ref_off = (fz_off + sizeof(T) * 2 * NF * NZP + 15) & ~size_t(15);
-    static constexpr size_t bytes = ref_off + sizeof(RefState<3>);
+    // FP32-bulk: the epilogue's own-cell operands, copied asynchronously at the
+    // start (the x+y residual, Delta_k, and in stage 3 U^n): [NF][NT] each
+    static constexpr size_t e_off = (ref_off + sizeof(RefState<3>) + 15) & ~size_t(15);
+    static constexpr size_t bytes = BULK ? e_off + 2 * sizeof(float) * NF * NT : ref_off + sizeof(RefState<3>);
+    static constexpr size_t bytes_un = BULK ? bytes + sizeof(double) * NF * NT : bytes;  // stage 3
 };
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
 }  // namespace zs
 
 template <bool BULK, int EPI, bool PD, int ST = 0>
@@ -52,6 +67,13 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
     const double dt = __longlong_as_double(dtbits);
     const double alpha = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][2])
                                    : __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
+    // FP32-bulk: alpha and b_k dt (an FP32 pair) converted once per block
+    __shared__ float s_al;
+    __shared__ float2 s_bdt;
+    if (BULK && threadIdx.x == 0) {
+        s_al = f64_to_f32(alpha);
+        s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+    }
 
     const int nx = a.n[0], nz = a.n[2];
     const long long N = a.N, sz = a.stride[2];
@@ -69,7 +91,21 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
 #pragma unroll
         for (int f = 0; f < NF; ++f) un[f] = __ldg(a.Un + f * N + cell);
     }
-    const T al = BULK ? (T)f64_to_f32(alpha) : (T)alpha;
+    // FP32-bulk: the epilogue's operands go out now as asynchronous copies into
+    // shared memory, so their latency hides behind the whole residual
+    float *e_acc = reinterpret_cast<float *>(smem + L::e_off);  // [NF][NT]
+    float *e_din = e_acc + NF * NT;                             // [NF][NT]
+    double *e_un = reinterpret_cast<double *>(e_din + NF * NT); // [NF][NT] (stage 3)
+    if (BULK && own) {
+        const float *acc = reinterpret_cast<const float *>(a.acc);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            cp_async4(e_acc + f * NT + threadIdx.x, acc + f * N + cell);
+            if (EPI == EPI_STAGE && ST > 0) cp_async4(e_din + f * NT + threadIdx.x, a.din + f * N + cell);
+            if (EPI == EPI_STAGE && ST == 2) cp_async8(e_un + f * NT + threadIdx.x, a.U + f * N + cell);
+        }
+    }
+    if (BULK) asm volatile("cp.async.commit_group;" ::: "memory");
     const double gm1 = a.gamma - 1.0;
     const bool interior = z0 >= 3 && z0 + TZ + 3 <= nz && x0 + TX <= nx;
 
@@ -111,6 +147,7 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
     };
     auto flux_store = [&](const T *q, int lx, int lz) {
         T fp[NF], fm[NF];
+        const T al = BULK ? (T)s_al : (T)alpha;  // (s_al is read after the reference state's barrier)
         if constexpr (BULK) split_flux_diff<3, 2, true>(q, ref, al, a.gm1_f, fp, fm);
         else split_flux_f64<3, 2, true>(q, al, gm1, fp, fm);
         const int o = (lz + 3) * TX + lx;
@@ -202,11 +239,13 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
 
     const T ihz = T(0.5) * (BULK ? (T)a.inv_h_f[2] : (T)a.inv_h[2]);  // face fluxes are twice F^
     const T *acc = reinterpret_cast<const T *>(a.acc);
+    if (BULK) asm volatile("cp.async.wait_group 0;" ::: "memory");  // this thread's own copies
     T r[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const T dz = Fz[f * NZI + (tz + 1) * TX + tx] - fzb[f];
-        r[f] = acc[f * N + cell] + (-dz * ihz);
+        if constexpr (BULK) r[f] = e_acc[f * NT + threadIdx.x] + (-dz * ihz);
+        else r[f] = acc[f * N + cell] + (-dz * ihz);
     }
     if (EPI == EPI_RHS) {
         if (own) {
@@ -224,7 +263,7 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
         bool bad = false;
         if (own) {
             // b_k dt and c_k = 2/3 as hi + lo pairs: no systematic coefficient rounding
-            const float2 bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+            const float2 bdt = s_bdt;
             constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
             constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
             float qn[NF];
@@ -232,12 +271,12 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
             for (int f = 0; f < NF; ++f) {
                 float t = bdt.y * r[f];
                 if (ST > 0) {
-                    const float dkf = __ldg(a.din + f * N + cell);
+                    const float dkf = e_din[f * NT + threadIdx.x];
                     t = fmaf(c_hi, dkf, fmaf(c_lo, dkf, t));
                 }
                 const float d = fmaf(bdt.x, r[f], t);
                 if (ST < 2) a.dout[f * N + cell] = d;
-                else a.Uout[f * N + cell] = __ldg(a.U + f * N + cell) + f32_to_f64(d);
+                else a.Uout[f * N + cell] = e_un[f * NT + threadIdx.x] + f32_to_f64(d);
                 qn[f] = hk[f] + d;  // the new state in FP32 (hk is the hi part of U^n)
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
@@ -276,15 +315,16 @@ template <bool BULK, int EPI, bool PD, int ST>
 static cudaError_t launch_z_st(const SweepArgs &a, cudaStream_t s)
 {
     using L = zs::Layout<BULK>;
+    constexpr size_t bytes = (BULK && EPI == EPI_STAGE && ST == 2) ? L::bytes_un : L::bytes;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_z<BULK, EPI, PD, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::bytes);
+                                             (int)bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((unsigned)((a.n[2] + zs::TZ - 1) / zs::TZ), (unsigned)((a.n[0] + zs::TX - 1) / zs::TX), (unsigned)a.n[1]);
-    k_z<BULK, EPI, PD, ST><<<grid, zs::NT, L::bytes, s>>>(a);
+    k_z<BULK, EPI, PD, ST><<<grid, zs::NT, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
