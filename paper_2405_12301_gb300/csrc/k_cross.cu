@@ -32,6 +32,9 @@ namespace wg {
 constexpr int XT = 256;       // threads per CTA of k_cross_vecs
 constexpr int VP = 32;        // padded vector length (largest rank)
 constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 consecutive rows hit distinct banks
+// FP32, stencil along the fiber: varying indices per block of the point-flux
+// path, so that each of its phases is one pass of the CTA's threads
+constexpr int fiber_vb(int threads, int chunk) { return threads / (chunk + 6) > 0 ? threads / (chunk + 6) : 1; }
 // k_cross is compiled for several (threads per CTA, samples per chunk) pairs;
 // the autotuner of api_cross.cu picks one, and the persistent grid size, per
 // workload class.  Until then variant 5 at 3 CTAs per SM runs: held to 80
@@ -164,6 +167,12 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
     T *C = reinterpret_cast<T *>(dyn);        // [5][CP][CS] contracted core rows of the chunk
     T *Cref = C + 5 * CP * CS;                // [5][CS]     chunk reference row (FP32, fd == mode)
     T *fixv = Cref + 5 * CS;                  // [5][CS]     the work item's fixed vector
+    // FP32, stencil along the fiber (role 1): per block of VB varying indices,
+    // the split fluxes of every chunk point, the face fluxes and the reference values
+    constexpr int VB = fiber_vb(XT, CH);
+    float *FL = reinterpret_cast<float *>(fixv + 5 * CS);  // [VB][CP][10]  f(+) then f(-), 5 fields
+    float *FF = FL + VB * CP * 10;                          // [VB][5][CH+1] face fluxes (doubled)
+    float *CT = FF + VB * 5 * (CH + 1);                     // [VB][5]       reference state (row i0)
     __shared__ long long s_item;
     const T eps = T(4) * (T)A.eps;  // split fluxes are formed doubled: 4 eps gives twice the WENO5 value
     const double gm1 = A.gamma - 1.0;
@@ -252,6 +261,111 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
             }
             __syncthreads();
 
+            if constexpr (!F64) if (role == 1) {
+                // The stencil moves along the fiber: neighbouring samples of one
+                // varying index share six of their seven points and one of their two
+                // faces, so each point's split flux and each face's WENO5(+/-) is
+                // formed once per block of VB varying indices (the values are the
+                // ones the per-sample path forms: the same dot products, split
+                // fluxes relative to row i0, and weno5_pm of the same windows).
+                for (long long vb0 = 0; vb0 < nvar; vb0 += VB) {
+                    // reference values (row i0) of the block's varying indices
+                    for (int u = threadIdx.x; u < VB * 5; u += XT) {
+                        const long long v = vb0 + u / 5;
+                        const int f = u % 5;
+                        float racc = 0.0f;
+                        if (v < nvar) {
+                            const float *lv = reinterpret_cast<const float *>(var) + (v * nsv) * 5 * VP + f * VP;
+                            float2 ra2 = bc2(0.0f);
+                            for (int x = 0; x < cl4; x += 4) {
+                                const float4 l4 = *reinterpret_cast<const float4 *>(lv + x);
+                                const float4 r4 = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(Cref) + f * CS + x);
+                                ra2 = fma2(make_float2(l4.z, l4.w), make_float2(r4.z, r4.w),
+                                           fma2(make_float2(l4.x, l4.y), make_float2(r4.x, r4.y), ra2));
+                            }
+                            racc = ra2.x + ra2.y;
+                        }
+                        CT[u] = racc;
+                    }
+                    __syncthreads();
+                    // split fluxes of every chunk point
+                    for (int u = threadIdx.x; u < VB * np; u += XT) {
+                        const int vl = u / np, pp = u - vl * np;
+                        const long long v = vb0 + vl;
+                        if (v >= nvar) continue;
+                        const float *lvb = reinterpret_cast<const float *>(var) + (v * nsv) * 5 * VP;
+                        float dq[5];
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) {
+                            const float *lv = lvb + f * VP;
+                            const float *crow = reinterpret_cast<const float *>(C) + (f * CP + pp) * CS;
+                            float2 a2 = bc2(0.0f);
+                            for (int x = 0; x < cl4; x += 4) {
+                                const float4 l4 = *reinterpret_cast<const float4 *>(lv + x);
+                                const float4 c4 = *reinterpret_cast<const float4 *>(crow + x);
+                                a2 = fma2(make_float2(l4.z, l4.w), make_float2(c4.z, c4.w),
+                                          fma2(make_float2(l4.x, l4.y), make_float2(c4.x, c4.y), a2));
+                            }
+                            dq[f] = a2.x + a2.y;
+                        }
+                        RefState<3> rs;
+                        const float *ct = CT + vl * 5;
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) { rs.hi[f] = ct[f]; rs.lo[f] = 0.0f; }
+                        {
+                            const float ir = 1.0f / ct[0];
+                            float ke = 0.0f;
+                            rs.rho = ct[0];
+#pragma unroll
+                            for (int e = 0; e < 3; ++e) {
+                                rs.m[e] = ct[1 + e];
+                                rs.u[e] = ct[1 + e] * ir;
+                                ke += rs.m[e] * rs.u[e];
+                            }
+                            rs.H = ct[4] + (float)gm1 * (ct[4] - 0.5f * ke);
+                        }
+                        float a5[5], b5[5];
+                        if (fd == 0) split_flux_diff<3, 0, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
+                        else if (fd == 1) split_flux_diff<3, 1, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
+                        else split_flux_diff<3, 2, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
+                        float *fl = FL + (vl * CP + pp) * 10;
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) { fl[f] = a5[f]; fl[5 + f] = b5[f]; }
+                    }
+                    __syncthreads();
+                    // face fluxes j = 0..cn (face j lies before sample j)
+                    for (int u = threadIdx.x; u < VB * (cn + 1); u += XT) {
+                        const int vl = u / (cn + 1), j = u - vl * (cn + 1);
+                        if (vb0 + vl >= nvar) continue;
+                        const float *fl = FL + (vl * CP + j) * 10;
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) {
+                            const float *P = fl + f, *M = fl + 5 + f;  // point k at [k * 10]
+                            FF[(vl * 5 + f) * (CH + 1) + j] =
+                                weno5_pm(make_float2(P[0], M[50]), make_float2(P[10], M[40]), make_float2(P[20], M[30]),
+                                         make_float2(P[30], M[20]), make_float2(P[40], M[10]), (float)eps);
+                        }
+                    }
+                    __syncthreads();
+                    for (int u = threadIdx.x; u < VB * cn; u += XT) {
+                        const int vl = u / cn, ii = u - vl * cn;
+                        const long long v = vb0 + vl;
+                        if (v >= nvar) continue;
+                        const int i = i0 + ii;
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) {
+                            const float *F = FF + (vl * 5 + f) * (CH + 1);
+                            const long long o = (long long)f * S.n_left * n * S.n_right + outbase_j + v * outstride_v +
+                                                (long long)i * S.n_right;
+                            out[o] = -(F[ii + 1] - F[ii]) * ih;
+                        }
+                    }
+                    // (the next block's first writes go to CT and FL, which no thread
+                    // reads after the barrier above)
+                }
+                __syncthreads();
+                continue;
+            }
             // samples (v, i): 7 stencil values per field, split fluxes, two interfaces
             for (long long u = threadIdx.x; u < nvar * CH; u += XT) {
                 const long long v = u / CH;
@@ -393,10 +507,12 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
     }
 }
 
-static size_t cross_dyn_bytes(bool f64, int chunk)
+static size_t cross_dyn_bytes(bool f64, int threads, int chunk)
 {
     const size_t e = f64 ? sizeof(double) : sizeof(float);
-    return e * (size_t)(5 * (chunk + 6) * CS + 2 * 5 * CS);
+    const int VB = fiber_vb(threads, chunk);
+    const size_t fiber = f64 ? 0 : sizeof(float) * (size_t)(VB * (chunk + 6) * 10 + VB * 5 * (chunk + 1) + VB * 5);
+    return e * (size_t)(5 * (chunk + 6) * CS + 2 * 5 * CS) + fiber;
 }
 
 int cross_vec_len() { return VP; }
@@ -417,7 +533,7 @@ static cudaError_t set_attr()
 {
     constexpr int XT_ = kCrossVariants[V].threads, CH_ = kCrossVariants[V].chunk, MB_ = kCrossVariants[V].minb;
     return cudaFuncSetAttribute(k_cross<F64, XT_, CH_, MB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cross_dyn_bytes(F64, CH_));
+                                (int)cross_dyn_bytes(F64, XT_, CH_));
 }
 
 // Shared-memory limits of every variant, set once before any launch (and so
@@ -440,7 +556,7 @@ template <bool F64, int V>
 static cudaError_t launch_main(const CrossArgs &a, long long blocks, cudaStream_t s)
 {
     constexpr int XT_ = kCrossVariants[V].threads, CH_ = kCrossVariants[V].chunk, MB_ = kCrossVariants[V].minb;
-    k_cross<F64, XT_, CH_, MB_><<<(unsigned)blocks, XT_, cross_dyn_bytes(F64, CH_), s>>>(a);
+    k_cross<F64, XT_, CH_, MB_><<<(unsigned)blocks, XT_, cross_dyn_bytes(F64, XT_, CH_), s>>>(a);
     return cudaGetLastError();
 }
 
