@@ -103,6 +103,9 @@ __global__ void k_step_begin(Ctl *c)
     }
     c->dt = dt;
     c->t_next = tn;
+    c->bdt[0] = f64_to_f32x2(dt);
+    c->bdt[1] = f64_to_f32x2(0.25 * dt);
+    c->bdt[2] = f64_to_f32x2(2.0 / 3.0 * dt);
     for (int k = 1; k < 4; ++k) {
         c->alpha[k] = 0ull;
         for (int e = 0; e < 3; ++e) c->alpha_dir[k][e] = 0ull;

@@ -215,22 +215,17 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
 
     const long long dtbits = __double_as_longlong(a.ctl->dt);
     if (a.check_dt && dtbits == 0) return;
-    const double dt = __longlong_as_double(dtbits);
-    __shared__ float2 s_bdt;  // b_k dt as an FP32 pair hi + lo
-    // the residual factors -(2/3) / h_d as FP32 pairs hi + lo: phase C's sums are
-    // 3/2 times the flux differences (the differences are stored as 1/4 of
-    // themselves, and the runs return 6/4 of the corrections), and a single
+    // b_k dt comes from the control block (set with dt, an FP32 pair hi + lo) and
+    // the residual factors -(2/3) / h_d from the host (SweepArgs::ih23): phase C's
+    // sums are 3/2 times the flux differences (the differences are stored as 1/4
+    // of themselves, and the runs return 6/4 of the corrections), and a single
     // rounded factor would bias every residual the same way
-    __shared__ float2 s_ih[2];
     __shared__ float2 s_al;  // the LF alpha of x and y in FP32 (converted once per block)
     __shared__ unsigned s_max[3];  // the block's wavespeed maxima (FP32 bit patterns)
     __shared__ int s_bad;
     if (threadIdx.x == 0) {
         s_max[0] = s_max[1] = s_max[2] = 0u;
         s_bad = 0;
-        if (EPI == EPI_STAGE) s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
-        s_ih[0] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[0]);
-        s_ih[1] = f64_to_f32x2(-(2.0 / 3.0) * a.inv_h[1]);
         const double alpha = __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
         s_al = make_float2(f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][0]) : alpha),
                            f64_to_f32(PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][1]) : alpha));
@@ -416,7 +411,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     // the factor pairs s_ih
     float2 r[2];  // the residual, fields (rho, m_x) and (m_y, E)
     {
-        const float2 ihx = s_ih[0], ihy = s_ih[1];
+        const float2 ihx = a.ih23[0], ihy = a.ih23[1];
         const int c = ty * TX + tx, cx = ty * CXP + tx;
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
@@ -441,7 +436,7 @@ __global__ void __launch_bounds__(xy2::NT, 5) k_xy2(const SweepArgs a)
     if (own) {
         // Delta = b_k dt R + c_k Delta_k with b_k dt and c_k = 2/3 as hi + lo pairs
         // (c_k = 1/4 is exact), so the coefficients carry no systematic rounding
-        const float2 bdt = s_bdt;
+        const float2 bdt = a.ctl->bdt[ST];
         constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
         constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
         float2 dn[2], qq[2];

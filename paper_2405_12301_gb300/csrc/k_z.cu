@@ -67,13 +67,10 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
     const double dt = __longlong_as_double(dtbits);
     const double alpha = PD ? __longlong_as_double((long long)a.ctl->alpha_dir[a.slot_in][2])
                                    : __longlong_as_double((long long)a.ctl->alpha[a.slot_in]);
-    // FP32-bulk: alpha and b_k dt (an FP32 pair) converted once per block
+    // FP32-bulk: alpha converted once per block (b_k dt comes from the control
+    // block as an FP32 pair, set with dt)
     __shared__ float s_al;
-    __shared__ float2 s_bdt;
-    if (BULK && threadIdx.x == 0) {
-        s_al = f64_to_f32(alpha);
-        s_bdt = f64_to_f32x2((ST == 0 ? 1.0 : (ST == 1 ? 0.25 : 2.0 / 3.0)) * dt);
-    }
+    if (BULK && threadIdx.x == 0) s_al = f64_to_f32(alpha);
 
     const int nx = a.n[0], nz = a.n[2];
     const long long N = a.N, sz = a.stride[2];
@@ -263,7 +260,7 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
         bool bad = false;
         if (own) {
             // b_k dt and c_k = 2/3 as hi + lo pairs: no systematic coefficient rounding
-            const float2 bdt = s_bdt;
+            const float2 bdt = a.ctl->bdt[ST];
             constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
             constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
             float qn[NF];

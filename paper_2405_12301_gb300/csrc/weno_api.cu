@@ -246,7 +246,12 @@ static SweepArgs base_args(weno_ctx *h)
     a.gamma_f = (float)h->p.gamma;
     a.gm1_f = (float)(h->p.gamma - 1.0);
     a.eps_f = (float)h->p.eps_weno;
-    for (int d = 0; d < 3; ++d) a.inv_h_f[d] = (float)a.inv_h[d];
+    for (int d = 0; d < 3; ++d) {
+        a.inv_h_f[d] = (float)a.inv_h[d];
+        const double x = -(2.0 / 3.0) * a.inv_h[d];
+        const float hi = (float)x;
+        a.ih23[d] = make_float2(hi, (float)(x - (double)hi));
+    }
     a.acc = h->acc;
     a.bcs = h->bcs_dev;
     // a scalar law has one wavespeed |f'(u)| for every direction

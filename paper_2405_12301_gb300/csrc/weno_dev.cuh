@@ -34,6 +34,7 @@ struct Ctl {
     long long max_steps;   // steps bound of the current run call
     int status;            // ST_* bits, latched
     int pad;
+    float2 bdt[3];         // b_k dt of stage k (1, 1/4, 2/3) as FP32 pairs hi + lo, set with dt
 };
 
 // ----------------------------------------------------------------- conversions

@@ -35,6 +35,7 @@ struct SweepArgs {
     double eps;
     float gamma_f, gm1_f, eps_f;  // the same constants in FP32, rounded on the host
     float inv_h_f[3];
+    float2 ih23[3];      // -(2/3) / h_d as FP32 pairs hi + lo (the 2D FP32-bulk residual factor)
     int stage;           // 0, 1, 2
     int slot_in;         // alpha slot used for the splitting
     int slot_out;        // alpha slot the EPI_STAGE epilogue publishes to
