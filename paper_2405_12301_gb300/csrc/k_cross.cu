@@ -35,6 +35,8 @@ constexpr int CS = VP + 4;    // shared-memory row stride: float4 reads of 8 con
 // FP32, stencil along the fiber: varying indices per block of the point-flux
 // path, so that each of its phases is one pass of the CTA's threads
 constexpr int fiber_vb(int threads, int chunk) { return threads / (chunk + 6) > 0 ? threads / (chunk + 6) : 1; }
+constexpr int FLS = 11;       // floats per point of the fiber path's split fluxes (10, padded odd:
+                              // consecutive points of a warp fall on distinct banks)
 // k_cross is compiled for several (threads per CTA, samples per chunk) pairs;
 // the autotuner of api_cross.cu picks one, and the persistent grid size, per
 // workload class.  Until then variant 5 at 3 CTAs per SM runs: held to 80
@@ -170,8 +172,8 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
     // FP32, stencil along the fiber (role 1): per block of VB varying indices,
     // the split fluxes of every chunk point, the face fluxes and the reference values
     constexpr int VB = fiber_vb(XT, CH);
-    float *FL = reinterpret_cast<float *>(fixv + 5 * CS);  // [VB][CP][10]  f(+) then f(-), 5 fields
-    float *FF = FL + VB * CP * 10;                          // [VB][5][CH+1] face fluxes (doubled)
+    float *FL = reinterpret_cast<float *>(fixv + 5 * CS);  // [VB][CP][FLS] f(+) then f(-), 5 fields
+    float *FF = FL + VB * CP * FLS;                         // [VB][5][CH+1] face fluxes (doubled)
     float *CT = FF + VB * 5 * (CH + 1);                     // [VB][5]       reference state (row i0)
     __shared__ long long s_item;
     const T eps = T(4) * (T)A.eps;  // split fluxes are formed doubled: 4 eps gives twice the WENO5 value
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
                         if (fd == 0) split_flux_diff<3, 0, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
                         else if (fd == 1) split_flux_diff<3, 1, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
                         else split_flux_diff<3, 2, true>(dq, rs, (float)alpha, (float)gm1, a5, b5);
-                        float *fl = FL + (vl * CP + pp) * 10;
+                        float *fl = FL + (vl * CP + pp) * FLS;
 #pragma unroll
                         for (int f = 0; f < 5; ++f) { fl[f] = a5[f]; fl[5 + f] = b5[f]; }
                     }
@@ -337,13 +339,14 @@ __global__ void __launch_bounds__(XT, MINB) k_cross(const CrossArgs A)
                     for (int u = threadIdx.x; u < VB * (cn + 1); u += XT) {
                         const int vl = u / (cn + 1), j = u - vl * (cn + 1);
                         if (vb0 + vl >= nvar) continue;
-                        const float *fl = FL + (vl * CP + j) * 10;
+                        const float *fl = FL + (vl * CP + j) * FLS;
 #pragma unroll
                         for (int f = 0; f < 5; ++f) {
-                            const float *P = fl + f, *M = fl + 5 + f;  // point k at [k * 10]
-                            FF[(vl * 5 + f) * (CH + 1) + j] =
-                                weno5_pm(make_float2(P[0], M[50]), make_float2(P[10], M[40]), make_float2(P[20], M[30]),
-                                         make_float2(P[30], M[20]), make_float2(P[40], M[10]), (float)eps);
+                            const float *P = fl + f, *M = fl + 5 + f;  // point j + k at [k * FLS]
+                            FF[(vl * 5 + f) * (CH + 1) + j] = weno5_pm(
+                                make_float2(P[0], M[5 * FLS]), make_float2(P[FLS], M[4 * FLS]),
+                                make_float2(P[2 * FLS], M[3 * FLS]), make_float2(P[3 * FLS], M[2 * FLS]),
+                                make_float2(P[4 * FLS], M[FLS]), (float)eps);
                         }
                     }
                     __syncthreads();
@@ -511,7 +514,7 @@ static size_t cross_dyn_bytes(bool f64, int threads, int chunk)
 {
     const size_t e = f64 ? sizeof(double) : sizeof(float);
     const int VB = fiber_vb(threads, chunk);
-    const size_t fiber = f64 ? 0 : sizeof(float) * (size_t)(VB * (chunk + 6) * 10 + VB * 5 * (chunk + 1) + VB * 5);
+    const size_t fiber = f64 ? 0 : sizeof(float) * (size_t)(VB * (chunk + 6) * FLS + VB * 5 * (chunk + 1) + VB * 5);
     return e * (size_t)(5 * (chunk + 6) * CS + 2 * 5 * CS) + fiber;
 }
 
