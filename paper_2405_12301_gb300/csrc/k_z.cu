@@ -35,12 +35,18 @@ template <bool BULK> struct Layout {
     // start (the x+y residual, Delta_k, and in stage 3 U^n): [NF][NT] each
     static constexpr size_t e_off = (ref_off + sizeof(RefState<3>) + 15) & ~size_t(15);
     static constexpr size_t bytes = BULK ? e_off + 2 * sizeof(float) * NF * NT : ref_off + sizeof(RefState<3>);
+    // (e_din holds a float4 per thread, the first four fields, then a float, E)
     static constexpr size_t bytes_un = BULK ? bytes + sizeof(double) * NF * NT : bytes;  // stage 3
 };
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async8(void *dst, const void *src)
@@ -98,8 +104,11 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             cp_async4(e_acc + f * NT + threadIdx.x, acc + f * N + cell);
-            if (EPI == EPI_STAGE && ST > 0) cp_async4(e_din + f * NT + threadIdx.x, a.din + f * N + cell);
             if (EPI == EPI_STAGE && ST == 2) cp_async8(e_un + f * NT + threadIdx.x, a.U + f * N + cell);
+        }
+        if (EPI == EPI_STAGE && ST > 0) {  // Delta_k: the float4 plane of the first four fields, then E
+            cp_async16(reinterpret_cast<float4 *>(e_din) + threadIdx.x, reinterpret_cast<const float4 *>(a.din) + cell);
+            cp_async4(e_din + 4 * NT + threadIdx.x, a.din1 + cell);
         }
     }
     if (BULK) asm volatile("cp.async.commit_group;" ::: "memory");
@@ -171,7 +180,7 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
     }
     if (BULK && EPI == EPI_STAGE && ST == 0 && own) {  // the split of U^n, read by stages 2 and 3
 #pragma unroll
-        for (int f = 0; f < NF; ++f) a.hl[f * N + cell] = make_float2(hk[f], lk[f]);
+        bulk_store_hl(a, cell, hk, lk);
     }
     if (BULK) {
         if (threadIdx.x < 32) {  // the tile's first cell is inside the grid
@@ -263,18 +272,22 @@ __global__ void __launch_bounds__(zs::NT, BULK ? 5 : 1) k_z(const SweepArgs a)
             const float2 bdt = a.ctl->bdt[ST];
             constexpr float c_hi = ST == 1 ? 0.25f : (float)(2.0 / 3.0);
             constexpr float c_lo = ST == 1 ? 0.0f : (float)(2.0 / 3.0 - (double)(float)(2.0 / 3.0));
-            float qn[NF];
+            float qn[NF], dn[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 float t = bdt.y * r[f];
                 if (ST > 0) {
-                    const float dkf = e_din[f * NT + threadIdx.x];
+                    const float dkf = f < 4 ? e_din[4 * threadIdx.x + f] : e_din[4 * NT + threadIdx.x];
                     t = fmaf(c_hi, dkf, fmaf(c_lo, dkf, t));
                 }
                 const float d = fmaf(bdt.x, r[f], t);
-                if (ST < 2) a.dout[f * N + cell] = d;
+                if (ST < 2) dn[f] = d;
                 else a.Uout[f * N + cell] = e_un[f * NT + threadIdx.x] + f32_to_f64(d);
                 qn[f] = hk[f] + d;  // the new state in FP32 (hk is the hi part of U^n)
+            }
+            if (ST < 2) {  // Delta_{k+1}: the float4 plane of the first four fields, then E
+                reinterpret_cast<float4 *>(a.dout)[(unsigned)cell] = make_float4(dn[0], dn[1], dn[2], dn[3]);
+                a.dout1[(unsigned)cell] = dn[4];
             }
             s = wavespeed_f32<3>(qn, a.gamma_f, bad);
             if (PD && !bad) dirspeeds_f32<3>(qn, a.gamma_f, sd);

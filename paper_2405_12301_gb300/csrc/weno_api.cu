@@ -292,7 +292,10 @@ static int enqueue_step(weno_ctx *h, double *U, cudaStream_t s)
     double *outs[3] = {h->S1, h->S2, U};
     // FP32-bulk (2D and 3D) keeps the split of U^n in S1 and the FP32 increments in S2
     const bool inc = h->dim >= 2 && bulk(h) && h->p.model == WENO_MODEL_EULER;
-    float *delta[2] = {reinterpret_cast<float *>(h->S2), reinterpret_cast<float *>(h->S2) + h->nf * h->N};
+    // 2D: Delta_1 and Delta_2 as float [cell][4] one after the other; 3D: their
+    // float4 planes (first four fields) one after the other, then their E planes
+    float *delta[2] = {reinterpret_cast<float *>(h->S2), reinterpret_cast<float *>(h->S2) + 4 * h->N};
+    float *delta1[2] = {reinterpret_cast<float *>(h->S2) + 8 * h->N, reinterpret_cast<float *>(h->S2) + 9 * h->N};
     for (int k = 0; k < 3; ++k) {
         SweepArgs a = base_args(h);
         a.U = inc ? U : in[k];
@@ -302,6 +305,8 @@ static int enqueue_step(weno_ctx *h, double *U, cudaStream_t s)
             a.hl = reinterpret_cast<float2 *>(h->S1);
             a.din = k > 0 ? delta[k - 1] : nullptr;
             a.dout = k < 2 ? delta[k] : nullptr;
+            a.din1 = h->dim == 3 && k > 0 ? delta1[k - 1] : nullptr;
+            a.dout1 = h->dim == 3 && k < 2 ? delta1[k] : nullptr;
         }
         a.stage = k;
         a.slot_in = k;

@@ -20,9 +20,13 @@ struct SweepArgs {
     double *Rout;        // output of EPI_RHS
     // 2D FP32-bulk stage state (k_xy2): the FP32 hi/lo split of U^n, written
     // by stage 1, and the FP32 increments Delta_k = U^(k) - U^n
-    float2 *hl;          // 2D: planes H, L of float4 [N] each; 3D: [nf][N]
-    const float *din;    // Delta_k read by stages 2 and 3
-    float *dout;         // Delta_{k+1} written by stages 1 and 2
+    // 2D: planes H, L of float4 [N] each; 3D: planes H4, L4 (float4 [N]: rho, m_x,
+    // m_y, m_z) then H1, L1 (float [N]: E)
+    float2 *hl;
+    const float *din;    // Delta_k read by stages 2 and 3 (3D: the float4 [N] plane of the first four fields)
+    float *dout;         // Delta_{k+1} written by stages 1 and 2 (3D: as din)
+    const float *din1;   // 3D: Delta_k of E (float [N])
+    float *dout1;        // 3D: Delta_{k+1} of E
     Ctl *ctl;
     long long N;         // cells per field (field stride)
     int n[3];
