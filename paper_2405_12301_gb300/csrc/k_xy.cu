@@ -435,6 +435,7 @@ static cudaError_t launch_xy_t(const SweepArgs &a, cudaStream_t s)
 
 cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
 {
+    if (bulk && a.N >= (1ll << 32)) return cudaErrorInvalidValue;  // the stage state is indexed in 32 bits
 #define X(D, B, E)                                            \
     if (dim == D && bulk == B && epi == E)                    \
         return a.per_dir ? launch_xy_t<D, B, E, true>(a, s)   \

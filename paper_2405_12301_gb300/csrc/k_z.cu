@@ -348,6 +348,7 @@ static cudaError_t launch_z_t(const SweepArgs &a, cudaStream_t s)
 
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s)
 {
+    if (bulk && a.N >= (1ll << 32)) return cudaErrorInvalidValue;  // the stage state is indexed in 32 bits
 #define X(B, E, P) \
     if (bulk == B && epi == E && (a.per_dir != 0) == P) return launch_z_t<B, E, P>(a, s);
     X(false, EPI_RHS, false) X(false, EPI_STAGE, false) X(true, EPI_RHS, false) X(true, EPI_STAGE, false)
