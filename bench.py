@@ -673,6 +673,17 @@ def pipe_peaks():
     return subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
 
 
+def tc_contract():
+    """Builds and runs the tensor-core contraction probe (probe/tc_contract.cu):
+    the cross evaluation's rank contraction as tcgen05.mma kind::tf32 with a
+    3-term split, against the same products on the FMA pipe."""
+    src = os.path.join(ROOT, "paper_2405_12301_gb300", "probe", "tc_contract.cu")
+    exe = os.path.join(ROOT, "paper_2405_12301_gb300", "_build", "tc_contract")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
+    return subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -682,7 +693,7 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cross", action="store_true", help="skip the TT cross-eval and scalar-law side measurements")
-    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar", "peaks", "step"],
+    ap.add_argument("--only", choices=["cross", "tt", "ttcross", "scalar", "peaks", "tc", "step"],
                     help="run one side measurement alone and print its JSON (for profiling)")
     ap.add_argument("--reps", type=int, default=5, help="timed calls of the --only measurement")
     args = ap.parse_args()
@@ -709,6 +720,9 @@ def main():
     if args.only:
         if args.only == "peaks":
             print(pipe_peaks())
+            return
+        if args.only == "tc":
+            print(tc_contract())
             return
         if args.only == "scalar":
             print(json.dumps(bench_scalar(weno, I, torch)))
