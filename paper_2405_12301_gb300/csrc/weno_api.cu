@@ -278,7 +278,8 @@ static int enqueue_sweeps(weno_ctx *h, SweepArgs a, int last, cudaStream_t s)
         else CK(h, launch(h, 4, s, [&] { return launch_xy(2, false, last, a, s); }));
     } else {
         CK(h, launch(h, 2, s, [&] { return launch_xy(3, bulk(h), EPI_STORE, a, s); }));
-        CK(h, launch(h, 5, s, [&] { return launch_z(bulk(h), last, a, s); }));
+        if (bulk(h)) CK(h, launch(h, 5, s, [&] { return launch_z2(last, a, s); }));
+        else CK(h, launch(h, 5, s, [&] { return launch_z(false, last, a, s); }));
     }
     return WENO_OK;
 }

@@ -56,6 +56,8 @@ cudaError_t launch_xy(int dim, bool bulk, int epi, const SweepArgs &a, cudaStrea
 cudaError_t launch_xy2(int epi, const SweepArgs &a, cudaStream_t s);
 // z direction of a 3D grid, adding the accumulator and ending the residual (EPI_RHS / EPI_STAGE).
 cudaError_t launch_z(bool bulk, int epi, const SweepArgs &a, cudaStream_t s);
+// z direction of a 3D FP32-bulk grid in pair-difference form (EPI_RHS / EPI_STAGE).
+cudaError_t launch_z2(int epi, const SweepArgs &a, cudaStream_t s);
 
 cudaError_t launch_alpha(int model, int dim, bool bulk, const double *U, long long N, double gamma, Ctl *ctl, int slot,
                          int per_dir, cudaStream_t s);
