@@ -63,9 +63,13 @@ typedef enum {
 typedef enum { WENO_BC_PERIODIC = 0, WENO_BC_TRANSMISSIVE = 1, WENO_BC_REFLECTIVE = 2, WENO_BC_INFLOW = 3 } weno_bc;
 
 /* WENO_FP64: every operation in FP64.  WENO_FP32_BULK: point fluxes, splitting
- * and reconstruction in FP32 on values taken relative to a reference state of
- * each tile line (stencil differences are formed before rounding to FP32);
- * the state, its stage combination and the conservation sums stay FP64. */
+ * and reconstruction in FP32 on stencil differences formed before rounding to
+ * FP32 (2D, and the z direction of 3D: differences of neighbouring points from
+ * their FP32 hi/lo splits; 1D and the x and y directions of 3D: values relative
+ * to a reference state of each tile); the SSP-RK3 stages run on FP32
+ * increments of the FP64 state (U^{n+1} = U^n + Delta_3 in FP64); the state,
+ * the maximum behind alpha, dt and the conservation sums stay FP64 (the
+ * per-cell wavespeeds are FP32). */
 typedef enum { WENO_FP64 = 0, WENO_FP32_BULK = 1 } weno_precision;
 
 /* Lax-Friedrichs constant.  WENO_ALPHA_GLOBAL_NORM: one global alpha = max
